@@ -1,0 +1,189 @@
+"""ctypes binding of the libunigs C ABI (include/unigs.h).
+
+Argument marshalling only: every function here forwards to the entry point
+of the same name; all arithmetic runs in the library's kernels.  Loading
+fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, Structure, c_char_p, c_float, c_int32, c_int64, c_size_t,
+                    c_uint32, c_void_p)
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libunigs.so")
+
+UNIGS_MAX_CAMS = 64
+UNIGS_TILE = 16
+UNIGS_MAX_SEM = 64
+UNIGS_FLAG_CENTER_DEPTH = 1
+
+UNIGS_OK = 0
+UNIGS_ERR_INVALID_ARG = 1
+UNIGS_ERR_CAPACITY = 2
+UNIGS_ERR_CUDA = 3
+UNIGS_ERR_NONFINITE = 4
+UNIGS_ERR_TIMEOUT = 5
+
+
+class unigs_camera(Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float),
+                ("cx", c_float), ("cy", c_float), ("R_wc", c_float * 9), ("t_wc", c_float * 3),
+                ("R_cw", c_float * 9), ("C", c_float * 3), ("z_near", c_float)]
+
+
+class unigs_gaussians(Structure):
+    _fields_ = [("n", c_int64), ("sh_degree", c_int32), ("n_sem", c_int32),
+                ("feat_dtype", c_int32), ("reserved", c_int32), ("mean", c_void_p),
+                ("quat", c_void_p), ("scale", c_void_p), ("opacity", c_void_p),
+                ("kfac", c_void_p), ("sh", c_void_p), ("sem", c_void_p)]
+
+
+class unigs_outputs(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("normal_g", c_void_p),
+                ("kmap", c_void_p), ("logits", c_void_p), ("T_final", c_void_p),
+                ("n_contrib", c_void_p)]
+
+
+class unigs_grad_outputs(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("normal_g", c_void_p),
+                ("kmap", c_void_p), ("logits", c_void_p)]
+
+
+class unigs_param_grads(Structure):
+    _fields_ = [("mean", c_void_p), ("quat", c_void_p), ("scale", c_void_p),
+                ("opacity", c_void_p), ("kfac", c_void_p), ("sh", c_void_p),
+                ("sem", c_void_p), ("accumulate", c_int32), ("reserved", c_int32)]
+
+
+class unigs_config(Structure):
+    _fields_ = [("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
+                ("lowpass", c_float), ("step1", c_int32), ("step2", c_int32),
+                ("lambda_", c_float), ("flags", c_uint32)]
+
+
+class unigs_plan(Structure):
+    _fields_ = [("n", c_int64), ("n_cams", c_int32), ("n_sem", c_int32),
+                ("sh_degree", c_int32), ("feat_dtype", c_int32), ("capacity", c_int64),
+                ("n_tiles", c_int64), ("n_pixels", c_int64),
+                ("tile_offset", c_int32 * (UNIGS_MAX_CAMS + 1)),
+                ("pixel_offset", c_int64 * (UNIGS_MAX_CAMS + 1)),
+                ("sort_passes", c_int32), ("reserved", c_int32), ("ws_bytes", c_size_t),
+                ("off", c_size_t * 16), ("cfg", unigs_config)]
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("unigs_config_default", None, [POINTER(unigs_config)]),
+    ("unigs_plan_init", c_int32, [POINTER(unigs_plan), POINTER(unigs_gaussians),
+                                  POINTER(unigs_camera), c_int32, POINTER(unigs_config), c_int64]),
+    ("unigs_workspace_bytes", c_size_t, [POINTER(unigs_plan)]),
+    ("unigs_preprocess", c_int32, [POINTER(unigs_plan), POINTER(unigs_gaussians),
+                                   POINTER(unigs_camera), c_void_p, c_void_p]),
+    ("unigs_bin_sort", c_int32, [POINTER(unigs_plan), c_void_p, POINTER(c_int64), c_void_p]),
+    ("unigs_render_fwd", c_int32, [POINTER(unigs_plan), POINTER(unigs_gaussians), c_void_p,
+                                   POINTER(unigs_outputs), c_void_p]),
+    ("unigs_depth_normal_fwd", c_int32, [POINTER(unigs_plan), POINTER(unigs_camera), c_void_p,
+                                         c_void_p, c_void_p]),
+    ("unigs_depth_normal_bwd", c_int32, [POINTER(unigs_plan), POINTER(unigs_camera), c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("unigs_render_bwd", c_int32, [POINTER(unigs_plan), POINTER(unigs_gaussians),
+                                   POINTER(unigs_camera), c_void_p, POINTER(unigs_outputs),
+                                   POINTER(unigs_grad_outputs), POINTER(unigs_param_grads),
+                                   c_void_p]),
+    ("unigs_status_poll", c_int32, [POINTER(unigs_plan), c_void_p, POINTER(c_int64), c_void_p]),
+    ("unigs_launches_per_step", c_int32, [POINTER(unigs_plan)]),
+    ("unigs_status_string", c_char_p, [c_int32]),
+]
+
+
+def exported_symbols():
+    """Names of the entry points declared in include/unigs.h."""
+    return [s[0] for s in _SIGS]
+
+
+def lib():
+    """The loaded libunigs (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libunigs.so is not built ({LIB_PATH}); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class UnigsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = lib().unigs_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else msg)
+        self.status = status
+
+
+def check(status: int, what: str = ""):
+    if status != UNIGS_OK:
+        raise UnigsError(status, what)
+
+
+# Thin wrappers with the C names ---------------------------------------------
+def unigs_config_default() -> unigs_config:
+    c = unigs_config()
+    lib().unigs_config_default(ctypes.byref(c))
+    return c
+
+
+def unigs_plan_init(plan, g, cams, n_cams, cfg, capacity) -> int:
+    return lib().unigs_plan_init(ctypes.byref(plan), ctypes.byref(g), cams, n_cams,
+                                 ctypes.byref(cfg) if cfg is not None else None, capacity)
+
+
+def unigs_workspace_bytes(plan) -> int:
+    return lib().unigs_workspace_bytes(ctypes.byref(plan))
+
+
+def unigs_preprocess(plan, g, cams, ws, stream) -> int:
+    return lib().unigs_preprocess(ctypes.byref(plan), ctypes.byref(g), cams, ws, stream)
+
+
+def unigs_bin_sort(plan, ws, n_out, stream) -> int:
+    return lib().unigs_bin_sort(ctypes.byref(plan), ws,
+                                ctypes.byref(n_out) if n_out is not None else None, stream)
+
+
+def unigs_render_fwd(plan, g, ws, out, stream) -> int:
+    return lib().unigs_render_fwd(ctypes.byref(plan), ctypes.byref(g), ws, ctypes.byref(out),
+                                  stream)
+
+
+def unigs_depth_normal_fwd(plan, cams, depth, normal_d, stream) -> int:
+    return lib().unigs_depth_normal_fwd(ctypes.byref(plan), cams, depth, normal_d, stream)
+
+
+def unigs_depth_normal_bwd(plan, cams, depth, g_normal_d, g_depth_in, g_depth_out,
+                           stream) -> int:
+    return lib().unigs_depth_normal_bwd(ctypes.byref(plan), cams, depth, g_normal_d,
+                                        g_depth_in, g_depth_out, stream)
+
+
+def unigs_render_bwd(plan, g, cams, ws, fwd, grad_out, grads, stream) -> int:
+    return lib().unigs_render_bwd(ctypes.byref(plan), ctypes.byref(g), cams, ws,
+                                  ctypes.byref(fwd), ctypes.byref(grad_out),
+                                  ctypes.byref(grads), stream)
+
+
+def unigs_status_poll(plan, ws, detail, stream) -> int:
+    return lib().unigs_status_poll(ctypes.byref(plan), ws,
+                                   ctypes.byref(detail) if detail is not None else None, stream)
+
+
+def unigs_launches_per_step(plan) -> int:
+    return lib().unigs_launches_per_step(ctypes.byref(plan))

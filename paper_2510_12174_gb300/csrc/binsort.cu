@@ -1,0 +1,295 @@
+// Binning: scan of tiles touched, key emission, stable LSD radix sort, ranges.
+//
+// The paper extends the tile pipeline of 3DGS (Sec. 3.4): each Gaussian is
+// duplicated once per tile its 3-sigma rectangle overlaps, keyed by
+// (global tile id << 32 | float32 bits of its camera-frame centre depth), and
+// the keys are sorted so that every tile holds a front-to-back list.  Depths
+// are > z_near > 0, so their bit patterns order like the values.  The sort is
+// a stable LSD radix sort over the used key bits (8-bit digits), so ties in
+// depth keep the emission order (Gaussian index): the order within a tile is
+// (depth, index).
+//
+// Every kernel reads the instance count from the workspace header, so the
+// whole sequence runs without a host round trip (CUDA-graph capture); grids
+// are sized from the plan's capacity and surplus blocks exit at once.
+#include "launch.h"
+
+namespace unigs {
+
+// ------------------------------------------------------------ block scan
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh_warp,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < (int)(blockDim.x >> 5) ? sh_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh_warp[lane] = s;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_base = wid ? sh_warp[wid - 1] : 0;
+    if (total) *total = sh_warp[(blockDim.x >> 5) - 1];
+    const uint32_t r = warp_base + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Phase 1: per-block sums of SCAN_ITEMS elements.
+__global__ void __launch_bounds__(256)
+    scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ partial) {
+    __shared__ uint32_t sw[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+    for (int j = threadIdx.x; j < SCAN_ITEMS; j += blockDim.x) {
+        const int64_t i = base + j;
+        if (i < n) s += in[i];
+    }
+    uint32_t tot;
+    block_exclusive_scan(s, sw, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Phase 2: exclusive scan of the block sums by one block; writes the total.
+__global__ void __launch_bounds__(1024)
+    scan_partials_kernel(uint32_t* __restrict__ partial, int64_t nb, uint32_t* __restrict__ total_out) {
+    __shared__ uint32_t sw[32];
+    uint32_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        const uint32_t v = i < nb ? partial[i] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, sw, &tot);
+        if (i < nb) partial[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+// Phase 3: scan within each block, offset by the scanned block sum.
+__global__ void __launch_bounds__(256)
+    scan_down_kernel(const uint32_t* __restrict__ in, int64_t n, const uint32_t* __restrict__ partial,
+                     uint32_t* __restrict__ out) {
+    __shared__ uint32_t sw[32];
+    constexpr int PER = SCAN_ITEMS / 256;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + (int64_t)threadIdx.x * PER;
+    uint32_t v[PER];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int64_t i = base + j;
+        v[j] = i < n ? in[i] : 0;
+        s += v[j];
+    }
+    uint32_t run = block_exclusive_scan(s, sw, nullptr) + partial[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int64_t i = base + j;
+        if (i < n) out[i] = run;
+        run += v[j];
+    }
+}
+
+static int scan_u32(const uint32_t* in, int64_t n, uint32_t* partial, uint32_t* out,
+                    uint32_t* total, cudaStream_t st) {
+    const int64_t nb = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    if (nb == 0) return 0;
+    scan_reduce_kernel<<<(unsigned)nb, 256, 0, st>>>(in, n, partial);
+    scan_partials_kernel<<<1, 1024, 0, st>>>(partial, nb, total);
+    scan_down_kernel<<<(unsigned)nb, 256, 0, st>>>(in, n, partial, out);
+    return 3;
+}
+
+// ------------------------------------------------------------ emission
+// Total = offsets[last] + touched[last]; checks the capacity and writes one
+// (key, value) per overlapped tile in (camera, Gaussian, tile row-major)
+// order.
+__global__ void __launch_bounds__(256)
+    emit_kernel(const CamTable* __restrict__ tab, int64_t n, int n_cams, int64_t capacity,
+                const uint2* __restrict__ rect, const uint32_t* __restrict__ touched,
+                const uint32_t* __restrict__ offs, const uint32_t* __restrict__ zbits,
+                WsHeader* __restrict__ hdr, unsigned long long* __restrict__ keys,
+                uint32_t* __restrict__ vals) {
+    const int64_t total = n * (int64_t)n_cams;
+    const uint64_t need = (uint64_t)offs[total - 1] + touched[total - 1];
+    if (need > (uint64_t)capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            hdr->need = need;
+            hdr->n_instances = 0;
+            set_status(hdr, UNIGS_ERR_CAPACITY);
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        hdr->n_instances = (uint32_t)need;
+        hdr->need = need;
+    }
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t cnt = touched[t];
+        if (cnt == 0) continue;
+        const int k = (int)(t / n);
+        const uint32_t g = (uint32_t)(t - (int64_t)k * n);
+        const DevCam& cam = tab->cam[k];
+        const uint2 r = rect[t];
+        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+        const unsigned long long zb = zbits[t];
+        uint32_t o = offs[t];
+        for (int ty = y0; ty < y1; ++ty)
+            for (int tx = x0; tx < x1; ++tx) {
+                const unsigned long long tile =
+                    (unsigned long long)(cam.tile_off + (int64_t)ty * cam.tiles_x + tx);
+                keys[o] = (tile << 32) | zb;
+                vals[o] = g;
+                ++o;
+            }
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+__device__ __forceinline__ uint32_t n_valid(const WsHeader* hdr) {
+    return hdr->status == UNIGS_ERR_CAPACITY ? 0u : hdr->n_instances;
+}
+
+// Per-block digit counts, stored digit-major: hist[d * nb + b].
+__global__ void __launch_bounds__(256)
+    radix_hist_kernel(const unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr,
+                      int shift, int nb, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t n = n_valid(hdr);
+    const int64_t base = (int64_t)blockIdx.x * SORT_ITEMS;
+    for (int j = threadIdx.x; j < SORT_ITEMS; j += 256) {
+        const int64_t i = base + j;
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter.  Warp w of the block owns keys [w*256, w*256+256) of the
+// block's chunk and walks them 32 at a time in order; __match_any_sync ranks
+// equal digits inside each step, a per-warp running count orders the steps,
+// and a prefix over warps orders the warps.
+__global__ void __launch_bounds__(256)
+    radix_scatter_kernel(const unsigned long long* __restrict__ kin,
+                         const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+                         uint32_t* __restrict__ vout, const uint32_t* __restrict__ scanned,
+                         const WsHeader* __restrict__ hdr, int shift, int nb) {
+    __shared__ uint32_t whist[8][256];
+    __shared__ uint32_t goff[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < 8 * 256; j += 256) (&whist[0][0])[j] = 0;
+    goff[threadIdx.x] = scanned[(int64_t)threadIdx.x * nb + blockIdx.x];
+    __syncthreads();
+    const uint32_t n = n_valid(hdr);
+    const int64_t base = (int64_t)blockIdx.x * SORT_ITEMS + w * 256;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    unsigned long long k[8];
+    uint32_t v[8], rank[8], dig[8];
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int64_t i = base + it * 32 + lane;
+        const bool ok = i < n;
+        k[it] = ok ? kin[i] : 0ull;
+        v[it] = ok ? vin[i] : 0u;
+        const uint32_t d = ok ? ((uint32_t)(k[it] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = (d < 256u) ? whist[w][d] : 0u;
+        __syncwarp();
+        if (d < 256u && lane == __ffs(peers) - 1) whist[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[it] = before + __popc(peers & lt_mask);
+        dig[it] = d;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < 8; ++w2) {
+            const uint32_t c = whist[w2][d];
+            whist[w2][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const uint32_t d = dig[it];
+        if (d < 256u) {
+            const uint32_t dst = goff[d] + whist[w][d] + rank[it];
+            kout[dst] = k[it];
+            vout[dst] = v[it];
+        }
+    }
+}
+
+// Per-tile [start, end) by boundary detection on the sorted keys.
+__global__ void __launch_bounds__(256)
+    ranges_kernel(const unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr,
+                  uint2* __restrict__ ranges) {
+    const uint32_t n = n_valid(hdr);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)(keys[i] >> 32);
+        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+        if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+    }
+}
+
+int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
+    const int64_t total = p.n * (int64_t)p.n_cams;
+    WsHeader* hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+    uint2* ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
+    int launches = 0;
+    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)p.n_tiles, st);
+    if (total == 0 || p.capacity == 0) return launches;
+    uint32_t* touched = ws_ptr<uint32_t>(ws, p, OFF_TOUCH);
+    uint32_t* offs = ws_ptr<uint32_t>(ws, p, OFF_OFFS);
+    uint32_t* scan_tmp = ws_ptr<uint32_t>(ws, p, OFF_SCAN);
+    launches += scan_u32(touched, total, scan_tmp, offs, nullptr, st);
+    unsigned long long* keys[2] = {ws_ptr<unsigned long long>(ws, p, OFF_KEYS0),
+                                   ws_ptr<unsigned long long>(ws, p, OFF_KEYS1)};
+    uint32_t* vals[2] = {ws_ptr<uint32_t>(ws, p, OFF_VALS0), ws_ptr<uint32_t>(ws, p, OFF_VALS1)};
+    {
+        const int64_t blocks = (total + 255) / 256;
+        const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+        emit_kernel<<<grid, 256, 0, st>>>(ws_ptr<CamTable>(ws, p, OFF_CAM), p.n, p.n_cams,
+                                          p.capacity, ws_ptr<uint2>(ws, p, OFF_RECT), touched,
+                                          offs, ws_ptr<uint32_t>(ws, p, OFF_ZBITS), hdr, keys[0],
+                                          vals[0]);
+        ++launches;
+    }
+    const int nb = (int)((p.capacity + SORT_ITEMS - 1) / SORT_ITEMS);
+    uint32_t* hist = ws_ptr<uint32_t>(ws, p, OFF_HIST);
+    for (int pass = 0; pass < p.sort_passes; ++pass) {
+        const int src = pass & 1, dst = src ^ 1;
+        radix_hist_kernel<<<nb, 256, 0, st>>>(keys[src], hdr, 8 * pass, nb, hist);
+        launches += 1 + scan_u32(hist, (int64_t)nb * 256, scan_tmp, hist, nullptr, st);
+        radix_scatter_kernel<<<nb, 256, 0, st>>>(keys[src], vals[src], keys[dst], vals[dst], hist,
+                                                 hdr, 8 * pass, nb);
+        ++launches;
+    }
+    const int fin = sorted_buffer(p);
+    {
+        const int64_t blocks = (p.capacity + 255) / 256;
+        const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+        ranges_kernel<<<grid, 256, 0, st>>>(keys[fin], hdr, ranges);
+        ++launches;
+    }
+    return launches;
+}
+
+}  // namespace unigs

@@ -1,0 +1,26 @@
+// Host-side launchers of the libunigs kernels (internal).
+#pragma once
+
+#include "unigs_internal.cuh"
+
+namespace unigs {
+
+// Each launcher returns the number of kernel launches it enqueued.
+int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTable& tab,
+                      void* ws, cudaStream_t st);
+int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st);
+int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
+                      const unigs_outputs& out, cudaStream_t st);
+int launch_depth_normal_fwd(const unigs_plan& p, const CamTable& tab, const float* depth,
+                            float* normal_d, cudaStream_t st);
+int launch_depth_normal_bwd(const unigs_plan& p, const CamTable& tab, const float* depth,
+                            const float* g_normal_d, const float* g_depth_in,
+                            float* g_depth_out, cudaStream_t st);
+int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
+                      const unigs_outputs& fwd, const unigs_grad_outputs& go,
+                      const unigs_param_grads& grads, cudaStream_t st);
+
+// Index of the buffer (0/1) that holds the sorted keys/values after the sort.
+inline int sorted_buffer(const unigs_plan& p) { return p.sort_passes & 1; }
+
+}  // namespace unigs

@@ -1,0 +1,257 @@
+// Preprocess: one thread per (camera, Gaussian).
+//
+// Discrete part (projected centre, EWA 2D covariance with the 0.3 px
+// low-pass, 3-sigma radius, tile rectangle, depth key) follows a fixed
+// float32 recipe: each operation is a single correctly rounded float32
+// operation in a fixed order (the __f*_rn intrinsics are never contracted
+// into FMAs), so the tile lists are bit-reproducible.  The paper extends the
+// tile pipeline of 3DGS without detailing it (Sec. 3.4).
+//
+// Continuous part: conic, a compensated projected centre (integer part plus
+// a float remainder, so alpha is evaluated from an accurate pixel offset),
+// SH colour (real SH basis to degree 3, colour = max(0, Y.h + 1/2)), and the
+// ray-ellipsoid setup of Sec. 3.2: v_s = S^-1 R^T (C - mu) and the map from
+// the camera-frame pixel ray d~ = ((u-cx)/fx, (v-cy)/fy, 1) to the local
+// scaled direction, d_s = S^-1 R^T R_cw d~ = M_c d~; plus N_w = R S^-1, which
+// maps a scaled-local surface point to the world-frame ellipsoid normal.
+#include "launch.h"
+#include "sh.cuh"
+
+namespace unigs {
+
+// Shorthands for the exactly-rounded, never-contracted float32 operations of
+// the binning recipe.
+#define RM(a, b) __fmul_rn((a), (b))
+#define RA(a, b) __fadd_rn((a), (b))
+#define RS(a, b) __fsub_rn((a), (b))
+
+struct Recipe {
+    float px, py, pz;       // camera-frame centre
+    float R[3][3];          // rotation of the normalised quaternion
+    float a, b, c, det;     // 2D covariance (+ low-pass) and determinant
+    float mx, my, radius;   // projected centre and 3-sigma radius
+    int x0, x1, y0, y1;     // tile rectangle [x0,x1) x [y0,y1)
+    bool valid;
+};
+
+__device__ __forceinline__ void rect_axis(float m, float r, int n_tiles, int* lo, int* hi) {
+    const float nt = (float)n_tiles;
+    float l = floorf(__fdiv_rn(RS(m, r), (float)TILE));
+    float h = ceilf(__fdiv_rn(RA(m, r), (float)TILE));
+    l = fminf(fmaxf(l, 0.f), nt);
+    h = fminf(fmaxf(h, 0.f), nt);
+    *lo = (int)l;
+    *hi = (int)h;
+}
+
+__device__ __forceinline__ void binning_recipe(const DevCam& cam, float mx_, float my_, float mz_,
+                                               float qw, float qx, float qy, float qz, float sx,
+                                               float sy, float sz, float lowpass, Recipe& o) {
+    const float* W = cam.R_wc;
+    o.px = RA(RA(RA(RM(W[0], mx_), RM(W[1], my_)), RM(W[2], mz_)), cam.t_wc[0]);
+    o.py = RA(RA(RA(RM(W[3], mx_), RM(W[4], my_)), RM(W[5], mz_)), cam.t_wc[1]);
+    o.pz = RA(RA(RA(RM(W[6], mx_), RM(W[7], my_)), RM(W[8], mz_)), cam.t_wc[2]);
+    const bool in_front = o.pz > cam.z_near;
+
+    const float qn2 = RA(RA(RA(RM(qw, qw), RM(qx, qx)), RM(qy, qy)), RM(qz, qz));
+    const bool qok = qn2 > 0.f;
+    const float qn = __fsqrt_rn(qn2);
+    const float w = __fdiv_rn(qw, qn), x = __fdiv_rn(qx, qn), y = __fdiv_rn(qy, qn),
+                z = __fdiv_rn(qz, qn);
+    float (&R)[3][3] = o.R;
+    R[0][0] = RS(1.f, RM(2.f, RA(RM(y, y), RM(z, z))));
+    R[0][1] = RM(2.f, RS(RM(x, y), RM(w, z)));
+    R[0][2] = RM(2.f, RA(RM(x, z), RM(w, y)));
+    R[1][0] = RM(2.f, RA(RM(x, y), RM(w, z)));
+    R[1][1] = RS(1.f, RM(2.f, RA(RM(x, x), RM(z, z))));
+    R[1][2] = RM(2.f, RS(RM(y, z), RM(w, x)));
+    R[2][0] = RM(2.f, RS(RM(x, z), RM(w, y)));
+    R[2][1] = RM(2.f, RA(RM(y, z), RM(w, x)));
+    R[2][2] = RS(1.f, RM(2.f, RA(RM(x, x), RM(y, y))));
+
+    const float s[3] = {sx, sy, sz};
+    float M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = RM(R[i][j], s[j]);
+    float S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            S[i][j] = RA(RA(RM(M[i][0], M[j][0]), RM(M[i][1], M[j][1])), RM(M[i][2], M[j][2]));
+            S[j][i] = S[i][j];
+        }
+    const float iz = __fdiv_rn(1.f, o.pz);
+    const float J00 = RM(cam.fx, iz);
+    const float J11 = RM(cam.fy, iz);
+    const float xz = RM(o.px, iz);
+    const float yz = RM(o.py, iz);
+    const float J02 = -RM(J00, xz);
+    const float J12 = -RM(J11, yz);
+    float T[2][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T[0][j] = RA(RM(J00, W[0 * 3 + j]), RM(J02, W[2 * 3 + j]));
+        T[1][j] = RA(RM(J11, W[1 * 3 + j]), RM(J12, W[2 * 3 + j]));
+    }
+    float U[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            U[i][j] = RA(RA(RM(T[i][0], S[0][j]), RM(T[i][1], S[1][j])), RM(T[i][2], S[2][j]));
+    const float c00 = RA(RA(RM(U[0][0], T[0][0]), RM(U[0][1], T[0][1])), RM(U[0][2], T[0][2]));
+    const float c01 = RA(RA(RM(U[0][0], T[1][0]), RM(U[0][1], T[1][1])), RM(U[0][2], T[1][2]));
+    const float c11 = RA(RA(RM(U[1][0], T[1][0]), RM(U[1][1], T[1][1])), RM(U[1][2], T[1][2]));
+    o.a = RA(c00, lowpass);
+    o.b = c01;
+    o.c = RA(c11, lowpass);
+    o.det = RS(RM(o.a, o.c), RM(o.b, o.b));
+    const bool det_ok = o.det > 0.f;
+    const float mid = RM(0.5f, RA(o.a, o.c));
+    const float lam = RA(mid, __fsqrt_rn(fmaxf(0.1f, RS(RM(mid, mid), o.det))));
+    o.radius = ceilf(RM(3.f, __fsqrt_rn(lam)));
+    o.mx = RA(RM(cam.fx, xz), cam.cx);
+    o.my = RA(RM(cam.fy, yz), cam.cy);
+    rect_axis(o.mx, o.radius, cam.tiles_x, &o.x0, &o.x1);
+    rect_axis(o.my, o.radius, cam.tiles_y, &o.y0, &o.y1);
+    o.valid = in_front && qok && det_ok && (o.x1 > o.x0) && (o.y1 > o.y0);
+}
+
+#undef RM
+#undef RA
+#undef RS
+
+// Projected centre f * (p / z) + c with a compensated evaluation, returned as
+// an integer-valued float plus remainder (hi + lo).
+__device__ __forceinline__ void compensated_center(float p, float z, float f, float c, float* hi,
+                                                   float* lo) {
+    const float q = __fdiv_rn(p, z);
+    const float r = fmaf(-q, z, p);           // exact: p - q z
+    const float q_lo = r / z;
+    const float prod = f * q;
+    const float e1 = fmaf(f, q, -prod);       // exact rounding error of f*q
+    const float sum = prod + c;
+    const float bb = sum - prod;
+    const float e2 = (prod - (sum - bb)) + (c - bb);  // two-sum error
+    const float tail = e2 + fmaf(f, q_lo, e1);
+    const float h = rintf(sum);
+    *hi = h;
+    *lo = (sum - h) + tail;
+}
+
+__global__ void __launch_bounds__(256)
+    preprocess_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab, int n_cams,
+                      float lowpass, float* __restrict__ rec, uint2* __restrict__ rect,
+                      uint32_t* __restrict__ touched, uint32_t* __restrict__ zbits) {
+    const int64_t n = g.n;
+    const int64_t total = n * (int64_t)n_cams;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t / n);
+        const int64_t i = t - (int64_t)k * n;
+        const DevCam& cam = tab->cam[k];
+        const float mux = __ldg(g.mean + i), muy = __ldg(g.mean + n + i),
+                    muz = __ldg(g.mean + 2 * n + i);
+        const float qw = __ldg(g.quat + i), qx = __ldg(g.quat + n + i),
+                    qy = __ldg(g.quat + 2 * n + i), qz = __ldg(g.quat + 3 * n + i);
+        const float sx = __ldg(g.scale + i), sy = __ldg(g.scale + n + i),
+                    sz = __ldg(g.scale + 2 * n + i);
+        Recipe rc;
+        binning_recipe(cam, mux, muy, muz, qw, qx, qy, qz, sx, sy, sz, lowpass, rc);
+        if (!rc.valid) {
+            touched[t] = 0;
+            rect[t] = make_uint2(0, 0);
+            zbits[t] = __float_as_uint(rc.pz);
+            continue;
+        }
+        touched[t] = (uint32_t)((rc.x1 - rc.x0) * (rc.y1 - rc.y0));
+        rect[t] = make_uint2((uint32_t)rc.x0 | ((uint32_t)rc.x1 << 16),
+                             (uint32_t)rc.y0 | ((uint32_t)rc.y1 << 16));
+        zbits[t] = __float_as_uint(rc.pz);
+
+        float o[REC_FLOATS];
+        compensated_center(rc.px, rc.pz, cam.fx, cam.cx, &o[R_MXH], &o[R_MXL]);
+        compensated_center(rc.py, rc.pz, cam.fy, cam.cy, &o[R_MYH], &o[R_MYL]);
+        o[R_OP] = __ldg(g.opacity + i);
+        o[R_K] = __ldg(g.kfac + i);
+        const float idet = 1.f / rc.det;
+        o[R_CON + 0] = rc.c * idet;
+        o[R_CON + 1] = -rc.b * idet;
+        o[R_CON + 2] = rc.a * idet;
+
+        // colour from SH, viewing direction mu - C
+        float dx = mux - cam.C[0], dy = muy - cam.C[1], dz = muz - cam.C[2];
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv; dy *= inv; dz *= inv;
+        float Y[16];
+        const int deg = g.sh_degree;
+        const int n_sh = (deg + 1) * (deg + 1);
+        sh_eval_basis(dx, dy, dz, deg, Y);
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        const size_t shb = (size_t)i * n_sh * 3;
+        for (int kk = 0; kk < n_sh; ++kk)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                col[ch] = fmaf(Y[kk], load_feat(g.sh, shb + kk * 3 + ch, g.feat_dtype), col[ch]);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) o[R_RGB + ch] = fmaxf(col[ch], 0.f);
+
+        // ray-ellipsoid setup (Sec. 3.2)
+        const float is[3] = {1.f / sx, 1.f / sy, 1.f / sz};
+        const float e[3] = {cam.C[0] - mux, cam.C[1] - muy, cam.C[2] - muz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // row a of S^-1 R^T: column a of R scaled by 1/s_a
+            const float ra0 = rc.R[0][a], ra1 = rc.R[1][a], ra2 = rc.R[2][a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                o[R_MC + a * 3 + b] =
+                    is[a] * fmaf(ra0, cam.R_cw[0 * 3 + b],
+                                 fmaf(ra1, cam.R_cw[1 * 3 + b], ra2 * cam.R_cw[2 * 3 + b]));
+            o[R_VS + a] = is[a] * fmaf(ra0, e[0], fmaf(ra1, e[1], ra2 * e[2]));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) o[R_NW + a * 3 + b] = rc.R[a][b] * is[b];
+        }
+        o[R_Z] = rc.pz;
+        o[34] = 0.f;
+        o[35] = 0.f;
+        float4* dst = reinterpret_cast<float4*>(rec + (size_t)t * REC_FLOATS);
+#pragma unroll
+        for (int q = 0; q < REC_FLOATS / 4; ++q)
+            dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    }
+}
+
+__global__ void init_kernel(CamTable tab, int n_cams, CamTable* __restrict__ dst,
+                            WsHeader* __restrict__ hdr) {
+    const int k = threadIdx.x;
+    if (k < n_cams) dst->cam[k] = tab.cam[k];
+    if (k == 0) {
+        hdr->status = 0;
+        hdr->n_instances = 0;
+        hdr->need = 0;
+    }
+}
+
+int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTable& tab,
+                      void* ws, cudaStream_t st) {
+    init_kernel<<<1, UNIGS_MAX_CAMS, 0, st>>>(tab, p.n_cams, ws_ptr<CamTable>(ws, p, OFF_CAM),
+                                              ws_ptr<WsHeader>(ws, p, OFF_HDR));
+    const int64_t total = p.n * (int64_t)p.n_cams;
+    int launches = 1;
+    if (total > 0) {
+        const int64_t blocks = (total + 255) / 256;
+        const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
+        preprocess_kernel<<<grid, 256, 0, st>>>(
+            g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.n_cams, p.cfg.lowpass,
+            ws_ptr<float>(ws, p, OFF_REC), ws_ptr<uint2>(ws, p, OFF_RECT),
+            ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS));
+        ++launches;
+    }
+    return launches;
+}
+
+}  // namespace unigs

@@ -1,0 +1,594 @@
+// Backward composite (Alg. 4) and preprocess backward.
+//
+// Kernel 1, one CTA per tile: each pixel restores T = T_final and walks its
+// list backwards from the last blended Gaussian, T <- T / (1 - alpha_i),
+// w_i = alpha_i T_i.  With G_i = sum_ch g_ch x_i,ch (upstream gradient dotted
+// with the Gaussian's features) and S_i = sum_{j>i} w_j G_j,
+//   dL/dx_i,ch = w_i g_ch            (Eq. gradiento, Eq. gradientk)
+//   dL/dalpha_i = T_i G_i - S_i / (1 - alpha_i).
+// The feature gradients of the depth (t_mid, supplement Sec. 2:
+// dt/db = -1/2a, dt/da = b/2a^2 with b = 2 v_s.d_s) and of the ellipsoid
+// normal flow to the per-(camera, Gaussian) ray-ellipsoid setup (M_c, v_s,
+// N_w); dL/dalpha flows to opacity, conic and projected centre.  The 32
+// lanes of a warp (32 pixels) are summed with a butterfly transpose-reduction
+// (lane L ends with component L) before one float32 atomic per lane.
+//
+// Kernel 2, one thread per Gaussian, loops over the cameras: conic -> 2D
+// covariance -> (J, Sigma) -> mean, rotation, scale (EWA chain of 3DGS);
+// M_c = S^-1 R^T R_cw, v_s = S^-1 R^T (C - mu), N_w = R S^-1 -> R, s, mu
+// (supplement Sec. 2: dL/ds_k = -(g_vs,k v_s,k + g_ds,k d_s,k)/s_k per ray,
+// dL/dmu = -R (g_vs / s)); colour -> SH coefficients and viewing direction;
+// then R(q^) -> q^ -> q through the tangent projection (I - q^ q^T)/|q|.
+#include "launch.h"
+#include "sh.cuh"
+#include "splat.cuh"
+
+namespace unigs {
+
+constexpr int BBATCH = 32;
+constexpr uint32_t BWAIT_LIMIT = 1u << 22;
+
+struct BwdParams {
+    const CamTable* tab;
+    int n_cams;
+    int n_sem;
+    int64_t n;
+    const float* rec;
+    const void* sem;
+    const uint32_t* vals;
+    const uint2* ranges;
+    WsHeader* hdr;
+    const float* T_final;
+    const uint32_t* n_contrib;
+    unigs_grad_outputs go;
+    float* grec;
+    float* gsem;
+    float alpha_min, alpha_max;
+    int center_depth;
+    int sem_bulk;
+};
+
+template <int NS, typename FT>
+struct BwdSmem {
+    float rec[2][BBATCH][REC_FLOATS];
+    FT sem[2][BBATCH][NS];
+    uint32_t ids[2][BBATCH];
+    uint64_t bar[2];
+    uint32_t max_last;
+};
+
+template <int NS, typename FT>
+__device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, FT>& S, int buf,
+                                          uint32_t first, int count, int cam) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(FT));
+    const uint32_t per = REC_FLOATS * 4 + (P.sem_bulk ? row_bytes : 0u);
+    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], per * (uint32_t)count);
+    __syncwarp();
+    if (lane < count) {
+        const uint32_t g = P.vals[first + lane];
+        S.ids[buf][lane] = g;
+        const size_t r = (size_t)cam * (size_t)P.n + g;
+        bulk_g2s(&S.rec[buf][lane][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
+        if (P.n_sem > 0) {
+            const FT* src = reinterpret_cast<const FT*>(P.sem) + (size_t)g * P.n_sem;
+            if (P.sem_bulk)
+                bulk_g2s(&S.sem[buf][lane][0], src, row_bytes, &S.bar[buf]);
+            else
+                for (int c = 0; c < P.n_sem; ++c) S.sem[buf][lane][c] = src[c];
+        }
+    }
+}
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+__device__ __forceinline__ void cross_acc(const float* a, const float* b, float* c) {
+    c[0] += a[1] * b[2] - a[2] * b[1];
+    c[1] += a[2] * b[0] - a[0] * b[2];
+    c[2] += a[0] * b[1] - a[1] * b[0];
+}
+
+template <int NS, typename FT>
+__global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BwdSmem<NS, FT>& S = *reinterpret_cast<BwdSmem<NS, FT>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t gtile = blockIdx.x;
+    int cam_idx;
+    const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
+    const int64_t ltile = gtile - cam.tile_off;
+    const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
+    const int u = tx * TILE + (tid & 15), v = ty * TILE + (tid >> 4);
+    const bool inside = u < cam.width && v < cam.height;
+    const float uf = (float)u, vf = (float)v;
+    const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
+    const int W = cam.width;
+    const int64_t HW = (int64_t)cam.height * W;
+    const int64_t pix = cam.pix_off;
+    const int64_t idx = (int64_t)v * W + u;
+
+    float T = 1.f;
+    uint32_t last = 0;
+    float g_rgb[3] = {0.f, 0.f, 0.f}, g_D = 0.f, g_N[3] = {0.f, 0.f, 0.f}, g_K = 0.f;
+    float g_O[NS];
+#pragma unroll
+    for (int c = 0; c < NS; ++c) g_O[c] = 0.f;
+    if (inside) {
+        T = P.T_final[pix + idx];
+        last = P.n_contrib[pix + idx];
+        if (P.go.rgb)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g_rgb[c] = P.go.rgb[pix * 3 + c * HW + idx];
+        if (P.go.depth) g_D = P.go.depth[pix + idx];
+        if (P.go.normal_g)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g_N[c] = P.go.normal_g[pix * 3 + c * HW + idx];
+        if (P.go.kmap) g_K = P.go.kmap[pix + idx];
+        if (P.go.logits)
+#pragma unroll
+            for (int c = 0; c < NS; ++c)
+                if (c < P.n_sem) g_O[c] = P.go.logits[pix * (int64_t)P.n_sem + c * HW + idx];
+    }
+
+    if (tid == 0) {
+        S.max_last = 0;
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+    }
+    for (int j = tid; j < 2 * BBATCH * NS; j += 256) (&S.sem[0][0][0])[j] = FT(0.f);
+    __syncthreads();
+    if (last) atomicMax(&S.max_last, last);
+    __syncthreads();
+    const int n_items = (int)S.max_last;
+    const int n_batches = (n_items + BBATCH - 1) / BBATCH;
+    const uint2 range = P.ranges[gtile];
+    if (n_batches == 0) return;
+    if (warp == 0)
+        bwd_issue<NS, FT>(P, S, 0, range.x + (n_batches - 1) * BBATCH,
+                          min(BBATCH, n_items - (n_batches - 1) * BBATCH), cam_idx);
+
+    float Sacc = 0.f;  // sum over already processed (later) Gaussians of w_j G_j
+    bool timed_out = false;
+    for (int it = 0; it < n_batches; ++it) {
+        const int b = n_batches - 1 - it;
+        const int buf = it & 1;
+        if (warp == 0 && b > 0)
+            bwd_issue<NS, FT>(P, S, buf ^ 1, range.x + (b - 1) * BBATCH, BBATCH, cam_idx);
+        if (!mbar_wait_bounded(&S.bar[buf], (uint32_t)(it >> 1) & 1u, BWAIT_LIMIT))
+            timed_out = true;
+        const int count = min(BBATCH, n_items - b * BBATCH);
+        if (!__all_sync(0xffffffffu, timed_out)) {
+            for (int j = count - 1; j >= 0; --j) {
+                const uint32_t pos = (uint32_t)(b * BBATCH + j);
+                const float* rc = &S.rec[buf][j][0];
+                float gv[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) gv[k] = 0.f;
+                float w = 0.f;
+                bool contrib = false;
+                if (!timed_out && pos < last) {
+                    float dx, dy, Gs;
+                    const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                    if (alpha >= P.alpha_min) {
+                        contrib = true;
+                        const float om = 1.f - alpha;
+                        T = T / om;
+                        w = alpha * T;
+                        PairGeom G;
+                        pair_geometry(rc, xt, yt, G);
+                        const float depth = P.center_depth ? rc[R_Z] : G.t;
+                        const float sg = G.inside ? -1.f : 1.f;
+                        float nh[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) nh[i] = G.m[i] * G.inv_m;
+                        // G_i: upstream gradient . features of Gaussian i
+                        const FT* srow = &S.sem[buf][j][0];
+                        float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
+                                   g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
+                                   sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]);
+#pragma unroll
+                        for (int c = 0; c < NS; ++c) Gi = fmaf(g_O[c], to_f(srow[c]), Gi);
+                        const float dL_da = T * Gi - Sacc / om;
+                        Sacc = fmaf(w, Gi, Sacc);
+                        // alpha = min(alpha_max, op * Gs)
+                        const bool clamped = rc[R_OP] * Gs > P.alpha_max;
+                        const float g_pow = clamped ? 0.f : dL_da * alpha;
+                        gv[G_OP] = clamped ? 0.f : dL_da * Gs;
+                        const float A = rc[R_CON], B = rc[R_CON + 1], C = rc[R_CON + 2];
+                        gv[G_CA] = -0.5f * dx * dx * g_pow;
+                        gv[G_CB] = -dx * dy * g_pow;
+                        gv[G_CC] = -0.5f * dy * dy * g_pow;
+                        gv[G_MX] = (A * dx + B * dy) * g_pow;
+                        gv[G_MY] = (C * dy + B * dx) * g_pow;
+                        gv[G_RGB] = w * g_rgb[0];
+                        gv[G_RGB + 1] = w * g_rgb[1];
+                        gv[G_RGB + 2] = w * g_rgb[2];
+                        gv[G_K] = w * g_K;
+                        const float* vs = rc + R_VS;
+                        const float* Nw = rc + R_NW;
+                        const float inv_a = 1.f / G.a;
+                        float g_ds[3] = {0.f, 0.f, 0.f}, g_vs[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
+                        // depth t_mid = -b'/a
+                        const float g_t = w * g_D;
+                        if (P.center_depth) {
+                            gv[G_Z] = g_t;
+                        } else {
+                            const float g_bp = -g_t * inv_a;
+                            g_a -= g_t * G.t * inv_a;
+#pragma unroll
+                            for (int i = 0; i < 3; ++i) {
+                                g_vs[i] = g_bp * G.ds[i];
+                                g_ds[i] = g_bp * vs[i];
+                            }
+                        }
+                        // normal n = sg * m / |m|, m = N_w p
+                        const float gn[3] = {w * g_N[0], w * g_N[1], w * g_N[2]};
+                        const float dgn = gn[0] * nh[0] + gn[1] * nh[1] + gn[2] * nh[2];
+                        float g_m[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) g_m[i] = sg * (gn[i] - dgn * nh[i]) * G.inv_m;
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) gv[G_NW + 3 * r + c] = g_m[r] * G.p[c];
+                        float g_p[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            g_p[c] = Nw[c] * g_m[0] + Nw[3 + c] * g_m[1] + Nw[6 + c] * g_m[2];
+                        // p = p_mid - sr h d_s, h = sqrt(disc)/a
+                        float g_disc = 0.f;
+                        if (G.hit) {
+                            const float g_h = -G.sr * (g_p[0] * G.ds[0] + g_p[1] * G.ds[1] +
+                                                       g_p[2] * G.ds[2]);
+#pragma unroll
+                            for (int i = 0; i < 3; ++i) g_ds[i] -= G.sr * G.h * g_p[i];
+                            g_disc = g_h * 0.5f * inv_a * inv_a / G.h;
+                            g_a -= g_h * G.h * inv_a;
+                        }
+                        // disc = a - |cv|^2
+                        g_a += g_disc;
+                        float g_cv[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) g_cv[i] = -2.f * g_disc * G.cv[i];
+                        // p_mid = (d_s x cv) / a
+                        const float g_q[3] = {g_p[0] * inv_a, g_p[1] * inv_a, g_p[2] * inv_a};
+                        cross_acc(G.cv, g_q, g_ds);
+                        cross_acc(g_q, G.ds, g_cv);
+                        g_a -= (g_p[0] * G.pm[0] + g_p[1] * G.pm[1] + g_p[2] * G.pm[2]) * inv_a;
+                        // cv = v_s x d_s
+                        cross_acc(G.ds, g_cv, g_vs);
+                        cross_acc(g_cv, vs, g_ds);
+                        // a = d_s . d_s
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) g_ds[i] = fmaf(2.f * g_a, G.ds[i], g_ds[i]);
+                        // d_s = M_c d~
+                        const float dt[3] = {xt, yt, 1.f};
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) gv[G_MC + 3 * r + c] = g_ds[r] * dt[c];
+                            gv[G_VS + r] = g_vs[r];
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const uint32_t g = S.ids[buf][j];
+                    const size_t rix = (size_t)cam_idx * (size_t)P.n + g;
+                    const float tot = warp_reduce_transpose32(gv, lane);
+                    if (tot != 0.f) atomicAdd(P.grec + rix * GREC_FLOATS + lane, tot);
+                    if (P.n_sem > 0) {
+                        const FT* srow = &S.sem[buf][j][0];
+                        (void)srow;
+#pragma unroll
+                        for (int h = 0; h < (NS + 31) / 32; ++h) {
+                            float sv[32];
+#pragma unroll
+                            for (int k = 0; k < 32; ++k)
+                                sv[k] = (h * 32 + k < NS) ? w * g_O[(h * 32 + k) % NS] : 0.f;
+                            const float st = warp_reduce_transpose32(sv, lane);
+                            const int c = h * 32 + lane;
+                            if (c < P.n_sem && st != 0.f)
+                                atomicAdd(P.gsem + (size_t)g * P.n_sem + c, st);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (timed_out && lane == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- kernel 2
+struct PreBwdParams {
+    const CamTable* tab;
+    int n_cams;
+    unigs_gaussians g;
+    const float* grec;
+    const uint32_t* touched;
+    unigs_param_grads out;
+    float lowpass;
+};
+
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams P) {
+    const int64_t n = P.g.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float mu[3] = {P.g.mean[i], P.g.mean[n + i], P.g.mean[2 * n + i]};
+        const float q0[4] = {P.g.quat[i], P.g.quat[n + i], P.g.quat[2 * n + i],
+                             P.g.quat[3 * n + i]};
+        const float s[3] = {P.g.scale[i], P.g.scale[n + i], P.g.scale[2 * n + i]};
+        const float qn = sqrtf(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
+        const float iq = 1.f / qn;
+        const float w = q0[0] * iq, x = q0[1] * iq, y = q0[2] * iq, z = q0[3] * iq;
+        float R[3][3];
+        R[0][0] = 1.f - 2.f * (y * y + z * z);
+        R[0][1] = 2.f * (x * y - w * z);
+        R[0][2] = 2.f * (x * z + w * y);
+        R[1][0] = 2.f * (x * y + w * z);
+        R[1][1] = 1.f - 2.f * (x * x + z * z);
+        R[1][2] = 2.f * (y * z - w * x);
+        R[2][0] = 2.f * (x * z - w * y);
+        R[2][1] = 2.f * (y * z + w * x);
+        R[2][2] = 1.f - 2.f * (x * x + y * y);
+        const float is[3] = {1.f / s[0], 1.f / s[1], 1.f / s[2]};
+        float M[3][3], Sig[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M[a][b] = R[a][b] * s[b];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                Sig[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
+
+        float g_mu[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {}, g_s[3] = {0.f, 0.f, 0.f};
+        float g_op = 0.f, g_k = 0.f;
+        const int deg = P.g.sh_degree;
+        const int n_sh = (deg + 1) * (deg + 1);
+        float g_sh[16][3];
+        for (int k = 0; k < 16; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+
+        for (int k = 0; k < P.n_cams; ++k) {
+            const size_t t = (size_t)k * (size_t)n + (size_t)i;
+            if (P.touched[t] == 0) continue;
+            const DevCam& cam = P.tab->cam[k];
+            float gr[GREC_FLOATS];
+            const float4* src = reinterpret_cast<const float4*>(P.grec + t * GREC_FLOATS);
+#pragma unroll
+            for (int q = 0; q < GREC_FLOATS / 4; ++q) {
+                const float4 f = src[q];
+                gr[4 * q] = f.x; gr[4 * q + 1] = f.y; gr[4 * q + 2] = f.z; gr[4 * q + 3] = f.w;
+            }
+            g_op += gr[G_OP];
+            g_k += gr[G_K];
+
+            // ---- colour -> SH and viewing direction
+            {
+                float d[3] = {mu[0] - cam.C[0], mu[1] - cam.C[1], mu[2] - cam.C[2]};
+                const float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const float il = 1.f / len;
+                d[0] *= il; d[1] *= il; d[2] *= il;
+                float Y[16];
+                sh_eval_basis(d[0], d[1], d[2], deg, Y);
+                float dY[16][3];
+                sh_eval_basis_grad(d[0], d[1], d[2], deg, dY);
+                float g_dir[3] = {0.f, 0.f, 0.f};
+                const size_t shb = (size_t)i * n_sh * 3;
+                for (int ch = 0; ch < 3; ++ch) {
+                    float raw = 0.5f;
+                    for (int kk = 0; kk < n_sh; ++kk)
+                        raw = fmaf(Y[kk], load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype), raw);
+                    if (raw < 0.f) continue;  // clamped at 0
+                    const float gc = gr[G_RGB + ch];
+                    for (int kk = 0; kk < n_sh; ++kk) {
+                        g_sh[kk][ch] = fmaf(Y[kk], gc, g_sh[kk][ch]);
+                        const float h = load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype) * gc;
+                        g_dir[0] = fmaf(h, dY[kk][0], g_dir[0]);
+                        g_dir[1] = fmaf(h, dY[kk][1], g_dir[1]);
+                        g_dir[2] = fmaf(h, dY[kk][2], g_dir[2]);
+                    }
+                }
+                const float dd = g_dir[0] * d[0] + g_dir[1] * d[1] + g_dir[2] * d[2];
+                for (int a = 0; a < 3; ++a) g_mu[a] += (g_dir[a] - dd * d[a]) * il;
+            }
+
+            // ---- projection, EWA covariance, conic
+            const float* Wr = cam.R_wc;
+            const float pc[3] = {Wr[0] * mu[0] + Wr[1] * mu[1] + Wr[2] * mu[2] + cam.t_wc[0],
+                                 Wr[3] * mu[0] + Wr[4] * mu[1] + Wr[5] * mu[2] + cam.t_wc[1],
+                                 Wr[6] * mu[0] + Wr[7] * mu[1] + Wr[8] * mu[2] + cam.t_wc[2]};
+            const float iz = 1.f / pc[2];
+            const float J00 = cam.fx * iz, J11 = cam.fy * iz;
+            const float J02 = -cam.fx * pc[0] * iz * iz, J12 = -cam.fy * pc[1] * iz * iz;
+            float Tm[2][3];
+            for (int j = 0; j < 3; ++j) {
+                Tm[0][j] = J00 * Wr[j] + J02 * Wr[6 + j];
+                Tm[1][j] = J11 * Wr[3 + j] + J12 * Wr[6 + j];
+            }
+            float U[2][3];
+            for (int a = 0; a < 2; ++a)
+                for (int j = 0; j < 3; ++j)
+                    U[a][j] = Tm[a][0] * Sig[0][j] + Tm[a][1] * Sig[1][j] + Tm[a][2] * Sig[2][j];
+            const float ca = U[0][0] * Tm[0][0] + U[0][1] * Tm[0][1] + U[0][2] * Tm[0][2] + P.lowpass;
+            const float cb = U[0][0] * Tm[1][0] + U[0][1] * Tm[1][1] + U[0][2] * Tm[1][2];
+            const float cc = U[1][0] * Tm[1][0] + U[1][1] * Tm[1][1] + U[1][2] * Tm[1][2] + P.lowpass;
+            const float det = ca * cc - cb * cb;
+            const float id2 = 1.f / (det * det);
+            const float gA = gr[G_CA], gB = gr[G_CB], gC = gr[G_CC];
+            // conic (A,B,C) = (c, -b, a) / det
+            const float g_ca = (-cc * cc * gA + cb * cc * gB + (det - ca * cc) * gC) * id2;
+            const float g_cb = (2.f * cb * cc * gA + (-det - 2.f * cb * cb) * gB + 2.f * ca * cb * gC) * id2;
+            const float g_cc = ((det - ca * cc) * gA + ca * cb * gB - ca * ca * gC) * id2;
+            // cov = T Sigma T^T: G_cov symmetric with the off-diagonal halved
+            const float Gc[2][2] = {{g_ca, 0.5f * g_cb}, {0.5f * g_cb, g_cc}};
+            // dL/dSigma = T^T G T
+            float gSig[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    gSig[a][b] = Tm[0][a] * (Gc[0][0] * Tm[0][b] + Gc[0][1] * Tm[1][b]) +
+                                 Tm[1][a] * (Gc[1][0] * Tm[0][b] + Gc[1][1] * Tm[1][b]);
+            // dL/dT = 2 G T Sigma
+            float gT[2][3];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 3; ++b)
+                    gT[a][b] = 2.f * (Gc[a][0] * U[0][b] + Gc[a][1] * U[1][b]);
+            const float gJ00 = gT[0][0] * Wr[0] + gT[0][1] * Wr[1] + gT[0][2] * Wr[2];
+            const float gJ02 = gT[0][0] * Wr[6] + gT[0][1] * Wr[7] + gT[0][2] * Wr[8];
+            const float gJ11 = gT[1][0] * Wr[3] + gT[1][1] * Wr[4] + gT[1][2] * Wr[5];
+            const float gJ12 = gT[1][0] * Wr[6] + gT[1][1] * Wr[7] + gT[1][2] * Wr[8];
+            float g_pc[3];
+            g_pc[0] = gJ02 * (-cam.fx * iz * iz) + gr[G_MX] * cam.fx * iz;
+            g_pc[1] = gJ12 * (-cam.fy * iz * iz) + gr[G_MY] * cam.fy * iz;
+            g_pc[2] = -gJ00 * cam.fx * iz * iz + gJ02 * 2.f * cam.fx * pc[0] * iz * iz * iz -
+                      gJ11 * cam.fy * iz * iz + gJ12 * 2.f * cam.fy * pc[1] * iz * iz * iz -
+                      gr[G_MX] * cam.fx * pc[0] * iz * iz - gr[G_MY] * cam.fy * pc[1] * iz * iz +
+                      gr[G_Z];
+            for (int a = 0; a < 3; ++a)
+                g_mu[a] += Wr[a] * g_pc[0] + Wr[3 + a] * g_pc[1] + Wr[6 + a] * g_pc[2];
+            // Sigma = M M^T, M = R S: dL/dM = 2 gSig M (gSig symmetric)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const float gM = 2.f * (gSig[a][0] * M[0][b] + gSig[a][1] * M[1][b] +
+                                            gSig[a][2] * M[2][b]);
+                    g_R[a][b] += gM * s[b];
+                    g_s[b] += gM * R[a][b];
+                }
+
+            // ---- ray-ellipsoid setup
+            const float e[3] = {cam.C[0] - mu[0], cam.C[1] - mu[1], cam.C[2] - mu[2]};
+            float g_e[3] = {0.f, 0.f, 0.f};
+            for (int a = 0; a < 3; ++a) {
+                // M_c[a][b] = (1/s_a) sum_k R[k][a] R_cw[k][b]
+                float acc_s = 0.f;
+                for (int b = 0; b < 3; ++b) {
+                    const float gq = gr[G_MC + 3 * a + b] * is[a];
+                    const float Q = R[0][a] * cam.R_cw[b] + R[1][a] * cam.R_cw[3 + b] +
+                                    R[2][a] * cam.R_cw[6 + b];
+                    acc_s += gq * Q;
+                    for (int kk = 0; kk < 3; ++kk) g_R[kk][a] += gq * cam.R_cw[3 * kk + b];
+                }
+                // v_s[a] = (1/s_a) sum_k R[k][a] e_k
+                const float gvl = gr[G_VS + a] * is[a];
+                const float vl = R[0][a] * e[0] + R[1][a] * e[1] + R[2][a] * e[2];
+                acc_s += gvl * vl;
+                for (int kk = 0; kk < 3; ++kk) {
+                    g_R[kk][a] += gvl * e[kk];
+                    g_e[kk] += R[kk][a] * gvl;
+                }
+                g_s[a] -= acc_s * is[a];
+            }
+            for (int a = 0; a < 3; ++a) g_mu[a] -= g_e[a];
+            // N_w[a][b] = R[a][b] / s_b
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const float gnw = gr[G_NW + 3 * a + b];
+                    g_R[a][b] += gnw * is[b];
+                    g_s[b] -= gnw * R[a][b] * is[b] * is[b];
+                }
+        }
+
+        // R(q^) -> q^ -> q
+        const float gw = 2.f * (-z * g_R[0][1] + y * g_R[0][2] + z * g_R[1][0] - x * g_R[1][2] -
+                                y * g_R[2][0] + x * g_R[2][1]);
+        const float gx = 2.f * (y * g_R[0][1] + z * g_R[0][2] + y * g_R[1][0] - 2.f * x * g_R[1][1] -
+                                w * g_R[1][2] + z * g_R[2][0] + w * g_R[2][1] - 2.f * x * g_R[2][2]);
+        const float gy = 2.f * (-2.f * y * g_R[0][0] + x * g_R[0][1] + w * g_R[0][2] + x * g_R[1][0] +
+                                z * g_R[1][2] - w * g_R[2][0] + z * g_R[2][1] - 2.f * y * g_R[2][2]);
+        const float gz = 2.f * (-2.f * z * g_R[0][0] - w * g_R[0][1] + x * g_R[0][2] + w * g_R[1][0] -
+                                2.f * z * g_R[1][1] + y * g_R[1][2] + x * g_R[2][0] + y * g_R[2][1]);
+        const float dq = gw * w + gx * x + gy * y + gz * z;
+        const float g_q[4] = {(gw - dq * w) * iq, (gx - dq * x) * iq, (gy - dq * y) * iq,
+                              (gz - dq * z) * iq};
+
+        const unigs_param_grads& O = P.out;
+        const bool acc = O.accumulate != 0;
+#define PUT(ptr, j, val) \
+    do { if (ptr) { if (acc) (ptr)[j] += (val); else (ptr)[j] = (val); } } while (0)
+        for (int a = 0; a < 3; ++a) {
+            PUT(O.mean, a * n + i, g_mu[a]);
+            PUT(O.scale, a * n + i, g_s[a]);
+        }
+        for (int a = 0; a < 4; ++a) PUT(O.quat, a * n + i, g_q[a]);
+        PUT(O.opacity, i, g_op);
+        PUT(O.kfac, i, g_k);
+        for (int kk = 0; kk < n_sh; ++kk)
+            for (int ch = 0; ch < 3; ++ch) PUT(O.sh, ((size_t)i * n_sh + kk) * 3 + ch, g_sh[kk][ch]);
+#undef PUT
+    }
+}
+
+template <int NS, typename FT>
+static void launch_bwd_t(const BwdParams& P, int64_t n_tiles, cudaStream_t st) {
+    const size_t smem = sizeof(BwdSmem<NS, FT>);
+    cudaFuncSetAttribute(render_bwd_kernel<NS, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    render_bwd_kernel<NS, FT><<<(unsigned)n_tiles, 256, smem, st>>>(P);
+}
+
+template <typename FT>
+static void launch_bwd_ft(const BwdParams& P, int64_t n_tiles, cudaStream_t st) {
+    if (P.n_sem <= 8)
+        launch_bwd_t<8, FT>(P, n_tiles, st);
+    else if (P.n_sem <= 16)
+        launch_bwd_t<16, FT>(P, n_tiles, st);
+    else if (P.n_sem <= 32)
+        launch_bwd_t<32, FT>(P, n_tiles, st);
+    else
+        launch_bwd_t<64, FT>(P, n_tiles, st);
+}
+
+int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
+                      const unigs_outputs& fwd, const unigs_grad_outputs& go,
+                      const unigs_param_grads& grads, cudaStream_t st) {
+    int launches = 0;
+    float* grec = ws_ptr<float>(ws, p, OFF_GREC);
+    cudaMemsetAsync(grec, 0, sizeof(float) * GREC_FLOATS * (size_t)p.n * p.n_cams, st);
+    if (grads.sem && !grads.accumulate && p.n_sem > 0)
+        cudaMemsetAsync(grads.sem, 0, sizeof(float) * (size_t)p.n * p.n_sem, st);
+    if (p.n_tiles > 0 && p.n > 0) {
+        BwdParams P;
+        P.tab = ws_ptr<CamTable>(ws, p, OFF_CAM);
+        P.n_cams = p.n_cams;
+        P.n_sem = p.n_sem;
+        P.n = p.n;
+        P.rec = ws_ptr<float>(ws, p, OFF_REC);
+        P.sem = g.sem;
+        P.vals = sorted_buffer(p) ? ws_ptr<uint32_t>(ws, p, OFF_VALS1)
+                                  : ws_ptr<uint32_t>(ws, p, OFF_VALS0);
+        P.ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
+        P.hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+        P.T_final = fwd.T_final;
+        P.n_contrib = fwd.n_contrib;
+        P.go = go;
+        P.grec = grec;
+        P.gsem = grads.sem;
+        P.alpha_min = p.cfg.alpha_min;
+        P.alpha_max = p.cfg.alpha_max;
+        P.center_depth = (p.cfg.flags & UNIGS_FLAG_CENTER_DEPTH) ? 1 : 0;
+        const size_t esz = p.feat_dtype ? 2 : 4;
+        P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * esz) % 16 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(g.sem) & 15) == 0);
+        if (p.feat_dtype)
+            launch_bwd_ft<__nv_bfloat16>(P, p.n_tiles, st);
+        else
+            launch_bwd_ft<float>(P, p.n_tiles, st);
+        ++launches;
+    }
+    if (p.n > 0) {
+        PreBwdParams Q;
+        Q.tab = ws_ptr<CamTable>(ws, p, OFF_CAM);
+        Q.n_cams = p.n_cams;
+        Q.g = g;
+        Q.grec = grec;
+        Q.touched = ws_ptr<uint32_t>(ws, p, OFF_TOUCH);
+        Q.out = grads;
+        Q.lowpass = p.cfg.lowpass;
+        const int64_t blocks = (p.n + 127) / 128;
+        const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+        preprocess_bwd_kernel<<<grid, 128, 0, st>>>(Q);
+        ++launches;
+    }
+    return launches;
+}
+
+}  // namespace unigs

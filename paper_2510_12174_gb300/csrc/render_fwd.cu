@@ -1,0 +1,261 @@
+// Forward composite (Alg. 2): one CTA of 256 threads per 16x16 tile, one
+// pixel per thread.
+//
+// Per pixel and per Gaussian of the tile's front-to-back list: alpha from the
+// 2D splat, skip below alpha_min, stop before the Gaussian that would bring T
+// below T_min; w = alpha T; accumulate RGB, the ray-ellipsoid midpoint depth
+// (Eq. midpoint, Eq. depth_render), the ellipsoid normal, k (Eq. t_render)
+// and the logits (Eq. semantic_render) in registers; save T_final and the
+// 1-based list position of the last blended Gaussian for the backward.
+//
+// Staging: the list is walked in batches of BATCH Gaussians.  Warp 0 issues
+// one bulk copy (TMA engine) per Gaussian record (144 B) and per semantic row
+// into a double-buffered shared-memory area completing on an mbarrier, so
+// batch b+1 streams in while batch b is composited.  A warp whose 32 pixels
+// are all finished skips the batch; the CTA leaves when all 256 are.
+#include "launch.h"
+#include "splat.cuh"
+
+namespace unigs {
+
+constexpr int BATCH = 32;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+struct FwdParams {
+    const CamTable* tab;
+    int n_cams;
+    int n_sem;
+    int64_t n;
+    const float* rec;
+    const void* sem;
+    const uint32_t* vals;
+    const uint2* ranges;
+    WsHeader* hdr;
+    unigs_outputs out;
+    float alpha_min, alpha_max, T_min;
+    int center_depth;
+    int sem_bulk;  // semantic rows are 16-byte multiples and aligned
+};
+
+template <int NS, typename FT>
+struct FwdSmem {
+    float rec[2][BATCH][REC_FLOATS];
+    FT sem[2][BATCH][NS];
+    uint64_t bar[2];
+};
+
+template <int NS, typename FT>
+__device__ __forceinline__ void issue_batch(const FwdParams& P, FwdSmem<NS, FT>& S, int buf,
+                                            uint32_t first, int count, int cam) {
+    // executed by warp 0 only
+    const int lane = threadIdx.x & 31;
+    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(FT));
+    const uint32_t per = REC_FLOATS * 4 + (P.sem_bulk ? row_bytes : 0u);
+    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], per * (uint32_t)count);
+    __syncwarp();
+    if (lane < count) {
+        const uint32_t g = P.vals[first + lane];
+        const size_t r = (size_t)cam * (size_t)P.n + g;
+        bulk_g2s(&S.rec[buf][lane][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
+        if (P.n_sem > 0) {
+            const FT* src = reinterpret_cast<const FT*>(P.sem) + (size_t)g * P.n_sem;
+            if (P.sem_bulk) {
+                bulk_g2s(&S.sem[buf][lane][0], src, row_bytes, &S.bar[buf]);
+            } else {
+                for (int c = 0; c < P.n_sem; ++c) S.sem[buf][lane][c] = src[c];
+            }
+        }
+    }
+}
+
+// co[c] += w * row[c] with 16-byte shared-memory loads.
+template <int NS>
+__device__ __forceinline__ void accumulate_row(const float* row, float w, float (&co)[NS]) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int c = 0; c < NS / 4; ++c) {
+        const float4 x = r4[c];
+        co[4 * c + 0] = fmaf(w, x.x, co[4 * c + 0]);
+        co[4 * c + 1] = fmaf(w, x.y, co[4 * c + 1]);
+        co[4 * c + 2] = fmaf(w, x.z, co[4 * c + 2]);
+        co[4 * c + 3] = fmaf(w, x.w, co[4 * c + 3]);
+    }
+}
+template <int NS>
+__device__ __forceinline__ void accumulate_row(const __nv_bfloat16* row, float w,
+                                               float (&co)[NS]) {
+    const uint4* r8 = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+    for (int c = 0; c < NS / 8; ++c) {
+        const uint4 x = r8[c];
+        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wv[q]));
+            co[8 * c + 2 * q] = fmaf(w, f.x, co[8 * c + 2 * q]);
+            co[8 * c + 2 * q + 1] = fmaf(w, f.y, co[8 * c + 2 * q + 1]);
+        }
+    }
+}
+
+template <int NS, typename FT>
+__global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FwdSmem<NS, FT>& S = *reinterpret_cast<FwdSmem<NS, FT>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int64_t gtile = blockIdx.x;
+    int cam_idx;
+    const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
+    const int64_t ltile = gtile - cam.tile_off;
+    const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
+    const int u = tx * TILE + (tid & 15), v = ty * TILE + (tid >> 4);
+    const bool inside = u < cam.width && v < cam.height;
+    const float uf = (float)u, vf = (float)v;
+    const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
+
+    const uint2 range = P.ranges[gtile];
+    const int n_items = (int)(range.y - range.x);
+    const int n_batches = (n_items + BATCH - 1) / BATCH;
+
+    // zero the semantic padding once (rows shorter than NS), init barriers
+    for (int j = tid; j < 2 * BATCH * NS; j += 256) (&S.sem[0][0][0])[j] = FT(0.f);
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0 && n_batches > 0)
+        issue_batch<NS, FT>(P, S, 0, range.x, min(BATCH, n_items), cam_idx);
+
+    float T = 1.f;
+    float crgb[3] = {0.f, 0.f, 0.f}, cdep = 0.f, cn[3] = {0.f, 0.f, 0.f}, ck = 0.f;
+    float co[NS];
+#pragma unroll
+    for (int c = 0; c < NS; ++c) co[c] = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    bool timed_out = false;
+
+    for (int b = 0; b < n_batches; ++b) {
+        const int buf = b & 1;
+        if (warp == 0 && b + 1 < n_batches)
+            issue_batch<NS, FT>(P, S, buf ^ 1, range.x + (b + 1) * BATCH,
+                                min(BATCH, n_items - (b + 1) * BATCH), cam_idx);
+        if (!mbar_wait_bounded(&S.bar[buf], (uint32_t)(b >> 1) & 1u, WAIT_LIMIT)) {
+            timed_out = true;
+        }
+        const int count = min(BATCH, n_items - b * BATCH);
+        const bool skip = __all_sync(0xffffffffu, done || timed_out);
+        if (!skip) {
+            for (int j = 0; j < count; ++j) {
+                if (done) continue;
+                const float* rc = &S.rec[buf][j][0];
+                float dx, dy, Gs;
+                const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                if (alpha < P.alpha_min) continue;
+                const float test_T = T * (1.f - alpha);
+                if (test_T < P.T_min) {
+                    done = true;
+                    continue;
+                }
+                const float w = alpha * T;
+                PairGeom G;
+                pair_geometry(rc, xt, yt, G);
+                const float depth = P.center_depth ? rc[R_Z] : G.t;
+                const float nsg = (G.inside ? -G.inv_m : G.inv_m) * w;
+                crgb[0] = fmaf(w, rc[R_RGB], crgb[0]);
+                crgb[1] = fmaf(w, rc[R_RGB + 1], crgb[1]);
+                crgb[2] = fmaf(w, rc[R_RGB + 2], crgb[2]);
+                cdep = fmaf(w, depth, cdep);
+                cn[0] = fmaf(nsg, G.m[0], cn[0]);
+                cn[1] = fmaf(nsg, G.m[1], cn[1]);
+                cn[2] = fmaf(nsg, G.m[2], cn[2]);
+                ck = fmaf(w, rc[R_K], ck);
+                accumulate_row<NS>(&S.sem[buf][j][0], w, co);
+                T = test_T;
+                last = (uint32_t)(b * BATCH + j + 1);
+            }
+        }
+        const int alive = __syncthreads_count(!done && !timed_out);
+        if (alive == 0) {
+            // drain the batch already in flight before leaving
+            if (b + 1 < n_batches)
+                mbar_wait_bounded(&S.bar[buf ^ 1], (uint32_t)((b + 1) >> 1) & 1u, WAIT_LIMIT);
+            break;
+        }
+    }
+    if (timed_out && (tid & 31) == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
+    if (!inside) return;
+    const int H = cam.height, W = cam.width;
+    const int64_t HW = (int64_t)H * W;
+    const int64_t pix = cam.pix_off;
+    const int64_t idx = (int64_t)v * W + u;
+    P.out.rgb[pix * 3 + 0 * HW + idx] = crgb[0];
+    P.out.rgb[pix * 3 + 1 * HW + idx] = crgb[1];
+    P.out.rgb[pix * 3 + 2 * HW + idx] = crgb[2];
+    P.out.depth[pix + idx] = cdep;
+    P.out.normal_g[pix * 3 + 0 * HW + idx] = cn[0];
+    P.out.normal_g[pix * 3 + 1 * HW + idx] = cn[1];
+    P.out.normal_g[pix * 3 + 2 * HW + idx] = cn[2];
+    P.out.kmap[pix + idx] = ck;
+    P.out.T_final[pix + idx] = T;
+    P.out.n_contrib[pix + idx] = last;
+    if (P.out.logits) {
+        float* lo = P.out.logits + pix * (int64_t)P.n_sem + idx;
+#pragma unroll
+        for (int c = 0; c < NS; ++c)
+            if (c < P.n_sem) lo[(int64_t)c * HW] = co[c];
+    }
+}
+
+template <int NS, typename FT>
+static void launch_fwd_t(const FwdParams& P, int64_t n_tiles, cudaStream_t st) {
+    const size_t smem = sizeof(FwdSmem<NS, FT>);
+    cudaFuncSetAttribute(render_fwd_kernel<NS, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    render_fwd_kernel<NS, FT><<<(unsigned)n_tiles, 256, smem, st>>>(P);
+}
+
+template <typename FT>
+static void launch_fwd_ft(const FwdParams& P, int64_t n_tiles, cudaStream_t st) {
+    if (P.n_sem <= 8)
+        launch_fwd_t<8, FT>(P, n_tiles, st);
+    else if (P.n_sem <= 16)
+        launch_fwd_t<16, FT>(P, n_tiles, st);
+    else if (P.n_sem <= 32)
+        launch_fwd_t<32, FT>(P, n_tiles, st);
+    else
+        launch_fwd_t<64, FT>(P, n_tiles, st);
+}
+
+int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
+                      const unigs_outputs& out, cudaStream_t st) {
+    if (p.n_tiles == 0) return 0;
+    FwdParams P;
+    P.tab = ws_ptr<CamTable>(ws, p, OFF_CAM);
+    P.n_cams = p.n_cams;
+    P.n_sem = p.n_sem;
+    P.n = p.n;
+    P.rec = ws_ptr<float>(ws, p, OFF_REC);
+    P.sem = g.sem;
+    P.vals = sorted_buffer(p) ? ws_ptr<uint32_t>(ws, p, OFF_VALS1) : ws_ptr<uint32_t>(ws, p, OFF_VALS0);
+    P.ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
+    P.hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+    P.out = out;
+    P.alpha_min = p.cfg.alpha_min;
+    P.alpha_max = p.cfg.alpha_max;
+    P.T_min = p.cfg.T_min;
+    P.center_depth = (p.cfg.flags & UNIGS_FLAG_CENTER_DEPTH) ? 1 : 0;
+    const size_t esz = p.feat_dtype ? 2 : 4;
+    P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * esz) % 16 == 0) &&
+                 ((reinterpret_cast<uintptr_t>(g.sem) & 15) == 0);
+    if (p.feat_dtype)
+        launch_fwd_ft<__nv_bfloat16>(P, p.n_tiles, st);
+    else
+        launch_fwd_ft<float>(P, p.n_tiles, st);
+    return 1;
+}
+
+}  // namespace unigs

@@ -1,0 +1,80 @@
+// Per-(pixel, Gaussian) math shared by the forward and backward composites.
+#pragma once
+
+#include "unigs_internal.cuh"
+
+namespace unigs {
+
+// alpha = min(alpha_max, opacity * exp(-1/2 D^T conic D)), D = pixel - centre,
+// with the centre held as integer part + remainder.  Written with
+// non-contractible intrinsics so the forward and the backward (which
+// recomputes alpha to undo T) obtain the same bits.
+__device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float uf, float vf,
+                                             float alpha_max, float* dx_out, float* dy_out,
+                                             float* gauss_out) {
+    const float dx = __fsub_rn(__fsub_rn(uf, rc[R_MXH]), rc[R_MXL]);
+    const float dy = __fsub_rn(__fsub_rn(vf, rc[R_MYH]), rc[R_MYL]);
+    const float A = rc[R_CON], B = rc[R_CON + 1], C = rc[R_CON + 2];
+    const float q = __fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(C, dy), dy));
+    const float power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(__fmul_rn(B, dx), dy));
+    const float G = __expf(power);
+    *dx_out = dx;
+    *dy_out = dy;
+    *gauss_out = G;
+    return fminf(alpha_max, __fmul_rn(rc[R_OP], G));
+}
+
+// a*b - c*d with Kahan's FMA compensation (error about one ulp of the result).
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+// Ray-ellipsoid quantities of one pair (Sec. 3.2 and the supplement's Sec. 1),
+// in the local scaled frame, for the camera-frame ray d~ = (xt, yt, 1):
+//   d_s = M_c d~, a = d_s.d_s, b' = v_s.d_s (b = 2b'), t_mid = -b'/a (the
+//   depth, because d~_z = 1), cv = v_s x d_s, disc = b'^2 - a c = a - |cv|^2
+//   (Lagrange's identity; free of the b^2 - 4ac cancellation),
+//   p_mid = (d_s x cv)/a (closest approach), h = sqrt(disc)/a (0 on a miss),
+//   p = p_mid - sr h d_s (entry point; exit point when the camera is inside,
+//   sr = -1), normal n = sign * normalize(N_w p).
+struct PairGeom {
+    float ds[3], a, bp, t, cv[3], disc, pm[3], h, p[3], m[3], inv_m, sr;
+    bool hit, inside;
+};
+
+__device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, float xt, float yt,
+                                              PairGeom& G) {
+    const float* M = rc + R_MC;
+    const float* vs = rc + R_VS;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G.ds[i] = fmaf(M[3 * i], xt, fmaf(M[3 * i + 1], yt, M[3 * i + 2]));
+    G.a = fmaf(G.ds[0], G.ds[0], fmaf(G.ds[1], G.ds[1], G.ds[2] * G.ds[2]));
+    G.bp = fmaf(vs[0], G.ds[0], fmaf(vs[1], G.ds[1], vs[2] * G.ds[2]));
+    const float inv_a = 1.f / G.a;
+    G.t = -G.bp * inv_a;
+    G.cv[0] = diff_of_products(vs[1], G.ds[2], vs[2], G.ds[1]);
+    G.cv[1] = diff_of_products(vs[2], G.ds[0], vs[0], G.ds[2]);
+    G.cv[2] = diff_of_products(vs[0], G.ds[1], vs[1], G.ds[0]);
+    const float cc = fmaf(G.cv[0], G.cv[0], fmaf(G.cv[1], G.cv[1], G.cv[2] * G.cv[2]));
+    G.disc = G.a - cc;
+    G.pm[0] = diff_of_products(G.ds[1], G.cv[2], G.ds[2], G.cv[1]) * inv_a;
+    G.pm[1] = diff_of_products(G.ds[2], G.cv[0], G.ds[0], G.cv[2]) * inv_a;
+    G.pm[2] = diff_of_products(G.ds[0], G.cv[1], G.ds[1], G.cv[0]) * inv_a;
+    const float vv = fmaf(vs[0], vs[0], fmaf(vs[1], vs[1], vs[2] * vs[2]));
+    G.inside = vv <= 1.f;
+    G.sr = G.inside ? -1.f : 1.f;
+    G.hit = G.disc > 0.f;
+    G.h = G.hit ? sqrtf(G.disc) * inv_a : 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G.p[i] = fmaf(-G.sr * G.h, G.ds[i], G.pm[i]);
+    const float* N = rc + R_NW;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        G.m[i] = fmaf(N[3 * i], G.p[0], fmaf(N[3 * i + 1], G.p[1], N[3 * i + 2] * G.p[2]));
+    G.inv_m = rsqrtf(fmaf(G.m[0], G.m[0], fmaf(G.m[1], G.m[1], G.m[2] * G.m[2])));
+}
+
+}  // namespace unigs

@@ -1,0 +1,174 @@
+// Internal definitions shared by the sm_103a kernels of libunigs.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "unigs.h"
+
+namespace unigs {
+
+constexpr int TILE = UNIGS_TILE;
+constexpr int TILE_PIX = TILE * TILE;
+
+// ----------------------------------------------------------------------------
+// Per-(camera, Gaussian) forward record written by the preprocess and staged
+// into shared memory by the composite kernels (36 floats = 144 bytes, a
+// multiple of 16 so a bulk copy can move it).
+//   [0..3]  projected centre split as integer part + remainder (x_hi, y_hi,
+//           x_lo, y_lo); m = hi + lo, hi an integer-valued float, |lo| <= 0.5
+//   [4]     opacity     [5] k (gradient factor)   [6..8] RGB
+//   [9..11] conic (A, B, C) of the inverse 2D covariance
+//   [12..20] M_c = S^-1 R^T R_cw (camera ray -> local scaled), row-major
+//   [21..23] v_s = S^-1 R^T (C - mu)
+//   [24..32] N_w = R S^-1 (scaled-local normal -> world), row-major
+//   [33]    camera-frame z of the centre   [34..35] unused
+// ----------------------------------------------------------------------------
+enum {
+    R_MXH = 0, R_MYH, R_MXL, R_MYL, R_OP, R_K, R_RGB, R_CON = 9, R_MC = 12,
+    R_VS = 21, R_NW = 24, R_Z = 33, REC_FLOATS = 36
+};
+
+// Per-(camera, Gaussian) intermediate gradient record (32 floats), filled by
+// atomics in the backward composite and consumed by the preprocess backward.
+enum {
+    G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_OP, G_RGB, G_MC = 9, G_VS = 18,
+    G_NW = 21, G_K = 30, G_Z = 31, GREC_FLOATS = 32
+};
+
+// Camera as the kernels see it (read from the workspace).
+struct DevCam {
+    int32_t width, height, tiles_x, tiles_y;
+    int64_t tile_off, pix_off;
+    float fx, fy, cx, cy;
+    float R_wc[9];
+    float t_wc[3];
+    float R_cw[9];
+    float C[3];
+    float z_near;
+    float pad[3];
+};
+static_assert(sizeof(DevCam) == 160, "DevCam layout");
+
+struct CamTable {
+    DevCam cam[UNIGS_MAX_CAMS];
+};
+
+// Device status block at the start of the workspace.
+struct WsHeader {
+    uint32_t status;       // unigs_status of the first device-side error
+    uint32_t n_instances;  // instances emitted (valid when not overflowed)
+    unsigned long long need;  // instances required (capacity errors)
+    uint32_t pad[60];
+};
+static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
+
+// Region indices into unigs_plan::off[].
+enum {
+    OFF_HDR = 0, OFF_CAM, OFF_REC, OFF_RECT, OFF_TOUCH, OFF_OFFS, OFF_ZBITS,
+    OFF_SCAN, OFF_KEYS0, OFF_KEYS1, OFF_VALS0, OFF_VALS1, OFF_HIST, OFF_RANGES,
+    OFF_GREC, OFF_END
+};
+
+constexpr int SORT_ITEMS = 2048;   // keys per sort block (256 threads x 8)
+constexpr int SCAN_ITEMS = 4096;   // elements per scan block (256 threads x 16)
+
+template <typename T>
+__host__ __device__ inline T* ws_ptr(void* ws, const unigs_plan& p, int region) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + p.off[region]);
+}
+
+__device__ inline const DevCam& cam_of_tile(const CamTable* tab, int n_cams, int64_t gtile,
+                                            int* cam_index) {
+    int lo = 0;
+    for (int k = 1; k < n_cams; ++k)
+        if (gtile >= tab->cam[k].tile_off) lo = k;
+    *cam_index = lo;
+    return tab->cam[lo];
+}
+
+__device__ inline void set_status(WsHeader* h, uint32_t code) {
+    atomicCAS(&h->status, 0u, code);
+}
+
+// Feature loads (float32 or bfloat16 storage, float32 math).
+__device__ __forceinline__ float load_feat(const void* base, size_t i, int bf16) {
+    if (bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[i]);
+    return reinterpret_cast<const float*>(base)[i];
+}
+
+// ----------------------------------------------------------------------------
+// mbarrier + bulk-copy (TMA engine, non-tensor) helpers, inline PTX.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Returns true once the phase with the given parity has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after max_iter polls and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t max_iter) {
+    for (uint32_t i = 0; i < max_iter; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 1D bulk copy global -> shared, completion counted on the mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ----------------------------------------------------------------------------
+// Warp transpose-reduction: every lane holds v[32]; afterwards lane L holds
+// the warp-wide sum of element L (recursive halving, 31 shuffles).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float warp_reduce_transpose32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int off = 16 >> step;
+        const int half = 16 >> step;  // current length is 2*half
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            float send = upper ? v[k] : v[k + half];
+            float keep = upper ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0];
+}
+
+}  // namespace unigs
