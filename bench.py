@@ -1,0 +1,419 @@
+"""Benchmark: RGB + depth + normal + semantic forward+backward views/s.
+
+Workload: the 1M-Gaussian synthetic room (log-scales N(-4.5, 1) clipped at -1,
+SH degree 3, 64 logits, k factor), seen at 1280x720.  One step renders and
+back-propagates a batch of 16 views on the orbit:
+
+* batched (the headline ``value``): one plan over the 16 cameras, SH and
+  logits stored as bfloat16, FP32 arithmetic, the whole preprocess + sort +
+  forward + normal-from-depth + backward sequence captured in one CUDA graph
+  and replayed per step;
+* per_view: the plain path, FP32 features, one camera per call sequence with
+  the instance count read back each call (16 sequences per step).
+
+Inputs (parameters, workspace, outputs) are far larger than the 129 MB L2, so
+no flush is needed between steps.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload.
+
+Multi-GPU: the path renders independent views, so N ranks are N replicas
+(weak scaling, no collective); ``value`` sums the views of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RGB+D+N+sem fwd+bwd views/s at 1M Gaussians 720p; batched vs per-view"
+N_GAUSS = 1_000_000
+N_VIEWS = 16
+WORKLOAD = "1M-Gaussian synthetic room, 16 orbit views at 1280x720, 64 logits, SH3, fwd+bwd"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 operations per (pixel, Gaussian) pair of the backward composite, counted
+# from its source (FMA = 2): alpha recomputation ~24 per evaluated pair; per
+# blended pair ~ 80 (geometry recompute) + 2*(8 + n_sem) (G_i dot) + ~190
+# (alpha, depth, normal chains) + 2*n_sem (semantic gradients).
+def bwd_flops(n_eval, n_blend, n_sem):
+    return 24.0 * n_eval + (80 + 2 * (8 + n_sem) + 190 + 2 * n_sem) * n_blend
+
+
+def fwd_flops(n_eval, n_blend, n_sem):
+    return 24.0 * n_eval + (80 + 2 * (11 + n_sem) + 10) * n_blend
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_2510_12174_gb300 import abi
+    from paper_2510_12174_gb300 import rasterizer as rz
+    from paper_2510_12174_gb300 import scenes
+
+    world, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ge.build()
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sc, cams = scenes.config3_orbit(N_VIEWS, n=args.n_gauss, feat_bf16=True)
+    n_sem = sc.n_sem
+    up = scenes.upstream_grads(cams, n_sem, seed=5)
+    keys = ("rgb", "depth", "normal_g", "kmap", "logits", "normal_d")
+    host_up = {k: torch.from_numpy(np.concatenate([a.ravel() for a in up[k]])).pin_memory()
+               for k in keys}
+    dev_up = {k: v.to(dev) for k, v in host_up.items()}
+
+    # ------------------------------------------------ batched (BF16, graph)
+    ds = rz.DeviceScene.from_scene(sc, device=dev, feat_bf16=True)
+    r = rz.Renderer(ds, cams)
+    out = r.forward()                      # sizes the capacity (one read-back)
+    torch.cuda.synchronize()
+    cap = int(r.last_instances * 1.15) + 65536
+    r = rz.Renderer(ds, cams, capacity=cap)
+    out = r.alloc_outputs()
+    grads = r.alloc_grads()
+    gbuf = torch.empty(r.n_pixels, device=dev)
+
+    def step():
+        r.forward(out, readback=False)
+        r.backward(out, dev_up, grads=grads, g_depth_buf=gbuf)
+
+    s_side = torch.cuda.Stream(device=dev)
+    s_side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_side):
+        for _ in range(2):
+            step()
+    torch.cuda.current_stream().wait_stream(s_side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    st, need = r.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} (need {need}) after warm-up")
+    n_eval, n_blend = r.stats()
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_all = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * N_VIEWS / (ms_all / 1000.0)
+
+    # stage times (same kernels, outside the graph, CUDA events on the stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    reps = max(2, min(5, args.steps))
+    acc = np.zeros(4)
+    for _ in range(reps):
+        ev[0].record(stream)
+        r.preprocess_and_sort(readback=False)
+        ev[1].record(stream)
+        abi.check(abi.unigs_render_fwd(r.plan, ds.struct(), r.ws.data_ptr(),
+                                       r._out_struct(out), r._stream()))
+        abi.check(abi.unigs_depth_normal_fwd(r.plan, r.cams, out["depth"].data_ptr(),
+                                             out["normal_d"].data_ptr(), r._stream()))
+        ev[2].record(stream)
+        abi.check(abi.unigs_depth_normal_bwd(r.plan, r.cams, out["depth"].data_ptr(),
+                                             dev_up["normal_d"].data_ptr(),
+                                             dev_up["depth"].data_ptr(), gbuf.data_ptr(),
+                                             r._stream()))
+        ev[3].record(stream)
+        go = abi.unigs_grad_outputs()
+        go.rgb, go.depth = dev_up["rgb"].data_ptr(), gbuf.data_ptr()
+        go.normal_g, go.kmap = dev_up["normal_g"].data_ptr(), dev_up["kmap"].data_ptr()
+        go.logits = dev_up["logits"].data_ptr()
+        pg = abi.unigs_param_grads()
+        for k in ("mean", "quat", "scale", "opacity", "kfac", "sh", "sem"):
+            setattr(pg, k, grads[k].data_ptr())
+        abi.check(abi.unigs_render_bwd(r.plan, ds.struct(), r.cams, r.ws.data_ptr(),
+                                       r._out_struct(out), go, pg, r._stream()))
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        acc += [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+    stage_ms = acc / reps
+
+    # ------------------------------------------------ e2e through host buffers
+    res_host = torch.empty(16, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    e2.record(stream)
+    for _ in range(e2e_steps):
+        for k in keys:
+            dev_up[k].copy_(host_up[k], non_blocking=True)
+        graph.replay()
+        res_host.copy_(grads["mean"].view(-1)[:16], non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / e2e_steps
+    h2d = sum(v.numel() * v.element_size() for v in host_up.values())
+
+    # ------------------------------------------------ per-view FP32 path
+    pv = None
+    if not args.skip_per_view:
+        ds32 = rz.DeviceScene.from_scene(sc, device=dev, feat_bf16=False)
+        rend = [rz.Renderer(ds32, [c]) for c in cams]
+        pv_up = []
+        offs = r.pixel_offsets()
+        for k in range(N_VIEWS):
+            d = {}
+            for key in keys:
+                ch = {"rgb": 3, "depth": 1, "normal_g": 3, "kmap": 1, "logits": n_sem,
+                      "normal_d": 3}[key]
+                d[key] = dev_up[key][offs[k] * ch: offs[k + 1] * ch]
+            pv_up.append(d)
+        outs = [rr.forward() for rr in rend]
+        gr32 = [rr.alloc_grads() for rr in rend]
+        torch.cuda.synchronize()
+
+        def pv_step():
+            for k, rr in enumerate(rend):
+                o = rr.forward(outs[k])
+                rr.backward(o, pv_up[k], grads=gr32[k])
+
+        for _ in range(max(1, args.warmup // 2)):
+            pv_step()
+        torch.cuda.synchronize()
+        pv_steps = max(1, args.steps // 2)
+        e0.record(stream)
+        for _ in range(pv_steps):
+            pv_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pv_ms = e0.elapsed_time(e1) / pv_steps
+        pv = {"value": N_VIEWS / (pv_ms / 1000.0), "unit": "views/s", "ms_per_step": pv_ms,
+              "dtype": "f32", "note": "one camera per call sequence, instance count read back"}
+        del rend, outs, gr32, ds32
+
+    peaks, src = _peaks()
+    clocks = clk.summary()
+    f_bwd = bwd_flops(n_eval, n_blend, n_sem)
+    bwd_ms = stage_ms[3]
+    sm_clock = (clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = f_bwd / (bwd_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": args.n_gauss, "views_per_step": N_VIEWS,
+                   "resolution": "1280x720", "n_sem": n_sem, "features": "bf16 storage",
+                   "path": "batched, one CUDA graph per step", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "per_view": pv,
+        "stage_ms": {"preprocess+bin_sort": stage_ms[0], "render_fwd+normal_d": stage_ms[1],
+                     "depth_normal_bwd": stage_ms[2], "render_bwd": stage_ms[3]},
+        "work": {"pairs_evaluated": n_eval, "pairs_blended": n_blend,
+                 "instances": int(r.last_instances or 0),
+                 "gaussian_pixel_evals_per_s": n_eval / (ms_all / 1000.0)},
+        "roofline": {"bound": "alu", "kernel": "render_bwd (composite backward + preprocess backward)",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"},
+        "e2e": {"value": N_VIEWS / (e2e_ms / 1000.0) * world, "unit": "views/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 64},
+        "gpu_launches": r.launches_per_step() * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_tiles, peaks_note=src)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+_CPU_SCENE = None
+
+
+def cpu_baseline(n_tiles: int, peaks_note: str = ""):
+    """The FP64 oracle, as it stands, on a band of tiles of one 720p view of the
+    same scene, forward + backward; scaled to whole views."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import raster as orr
+    from paper_2510_12174_gb300 import scenes
+
+    global _CPU_SCENE
+    if _CPU_SCENE is None:
+        sc, cams = scenes.config3_orbit(1, n=N_GAUSS, feat_bf16=True)
+        _CPU_SCENE = (sc, cams, scenes.upstream_grads(cams, sc.n_sem, seed=5))
+    sc, cams, up = _CPU_SCENE
+    cam = cams[0]
+    TX = (cam.width + 15) // 16
+    TY = (cam.height + 15) // 16
+    row = TY // 2
+    tiles = [row * TX + (TX // 2 - n_tiles // 2) + j for j in range(n_tiles)]
+    t0 = time.perf_counter()
+    b = oracle.bin_cameras_fast(sc, cams)
+    params = orr.Params.from_scene(sc, requires_grad=True)
+    prep = orr.preprocess(params, cam)
+    t1 = time.perf_counter()
+    tot = torch.zeros((), dtype=torch.float64)
+    r = orr.render_camera(prep, cam, b, 0, tiles=tiles)
+    for key, name in (("rgb", "rgb"), ("depth", "depth"), ("normal", "normal_g"),
+                      ("kmap", "kmap"), ("logits", "logits")):
+        g = torch.as_tensor(np.asarray(up[name][0], dtype=np.float64))
+        tot = tot + (r[key] * g).sum()
+    tot.backward()
+    t2 = time.perf_counter()
+    per_view = (t1 - t0) + (t2 - t1) * (TX * TY) / len(tiles)
+    return {"value": 1.0 / per_view, "unit": "views/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(tiles)} of {TX * TY} tiles of one 1280x720 view (1M Gaussians), "
+                      f"fwd+bwd, plus the full preprocess and binning; scaled by tile count "
+                      f"({t2 - t0:.1f} s measured)"}
+
+
+def run_reference(args):
+    world, rank = _dist()
+    if rank != 0:
+        return
+    import torch
+    t0 = time.perf_counter()
+    res = []
+    for _ in range(max(1, args.steps)):
+        res.append(cpu_baseline(args.cpu_tiles))
+    v = statistics.median(x["value"] for x in res)
+    cb = dict(res[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "views/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "note": "FP64 CPU oracle on a tile band"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "views/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
+    ap.add_argument("--cpu-tiles", type=int, default=12)
+    ap.add_argument("--skip-per-view", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

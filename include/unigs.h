@@ -240,10 +240,16 @@ unigs_status unigs_render_bwd(const unigs_plan* plan, const unigs_gaussians* g,
 unigs_status unigs_status_poll(const unigs_plan* plan, const void* ws, int64_t* detail,
                                unigs_stream stream);
 
-/* Number of kernel launches the last successful call sequence made inside
- * each entry point is fixed per plan; this returns the launches of one
- * preprocess + bin_sort + render_fwd + depth_normal_fwd + depth_normal_bwd +
- * render_bwd sequence. */
+/* Work counters of the last unigs_render_fwd on this workspace (synchronises
+ * the stream): the (pixel, Gaussian) pairs whose alpha was evaluated, and the
+ * pairs blended (alpha >= alpha_min before the transmittance stop).  These
+ * are the units of the compositing cost model.  Cleared by unigs_preprocess. */
+unigs_status unigs_stats_poll(const unigs_plan* plan, const void* ws, int64_t* pairs_evaluated,
+                              int64_t* pairs_blended, unigs_stream stream);
+
+/* The number of kernels one preprocess + bin_sort + render_fwd +
+ * depth_normal_fwd + depth_normal_bwd + render_bwd sequence launches for this
+ * plan (the count is fixed by the plan). */
 int32_t unigs_launches_per_step(const unigs_plan* plan);
 
 const char* unigs_status_string(unigs_status s);

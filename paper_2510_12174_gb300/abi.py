@@ -95,6 +95,8 @@ _SIGS = [
                                    POINTER(unigs_grad_outputs), POINTER(unigs_param_grads),
                                    c_void_p]),
     ("unigs_status_poll", c_int32, [POINTER(unigs_plan), c_void_p, POINTER(c_int64), c_void_p]),
+    ("unigs_stats_poll", c_int32, [POINTER(unigs_plan), c_void_p, POINTER(c_int64),
+                                   POINTER(c_int64), c_void_p]),
     ("unigs_launches_per_step", c_int32, [POINTER(unigs_plan)]),
     ("unigs_status_string", c_char_p, [c_int32]),
 ]
@@ -183,6 +185,11 @@ def unigs_render_bwd(plan, g, cams, ws, fwd, grad_out, grads, stream) -> int:
 def unigs_status_poll(plan, ws, detail, stream) -> int:
     return lib().unigs_status_poll(ctypes.byref(plan), ws,
                                    ctypes.byref(detail) if detail is not None else None, stream)
+
+
+def unigs_stats_poll(plan, ws, n_eval, n_blend, stream) -> int:
+    return lib().unigs_stats_poll(ctypes.byref(plan), ws, ctypes.byref(n_eval),
+                                  ctypes.byref(n_blend), stream)
 
 
 def unigs_launches_per_step(plan) -> int:

@@ -232,6 +232,20 @@ unigs_status unigs_status_poll(const unigs_plan* plan, const void* ws, int64_t* 
     return (unigs_status)h.status;
 }
 
+unigs_status unigs_stats_poll(const unigs_plan* plan, const void* ws, int64_t* pairs_evaluated,
+                              int64_t* pairs_blended, unigs_stream stream) {
+    if (!plan || !ws) return UNIGS_ERR_INVALID_ARG;
+    WsHeader h;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, ws_ptr<WsHeader>(const_cast<void*>(ws), *plan, OFF_HDR), 64,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return UNIGS_ERR_CUDA;
+    if (pairs_evaluated) *pairs_evaluated = (int64_t)h.n_eval;
+    if (pairs_blended) *pairs_blended = (int64_t)h.n_blend;
+    return UNIGS_OK;
+}
+
 int32_t unigs_launches_per_step(const unigs_plan* plan) {
     if (!plan) return 0;
     const int per_pass = 1 + 3 + 1;

@@ -15,6 +15,7 @@
 // scaled direction, d_s = S^-1 R^T R_cw d~ = M_c d~; plus N_w = R S^-1, which
 // maps a scaled-local surface point to the world-frame ellipsoid normal.
 #include "launch.h"
+#include "ff.cuh"
 #include "sh.cuh"
 
 namespace unigs {
@@ -124,22 +125,92 @@ __device__ __forceinline__ void binning_recipe(const DevCam& cam, float mx_, flo
 #undef RA
 #undef RS
 
-// Projected centre f * (p / z) + c with a compensated evaluation, returned as
-// an integer-valued float plus remainder (hi + lo).
-__device__ __forceinline__ void compensated_center(float p, float z, float f, float c, float* hi,
-                                                   float* lo) {
-    const float q = __fdiv_rn(p, z);
-    const float r = fmaf(-q, z, p);           // exact: p - q z
-    const float q_lo = r / z;
-    const float prod = f * q;
-    const float e1 = fmaf(f, q, -prod);       // exact rounding error of f*q
-    const float sum = prod + c;
-    const float bb = sum - prod;
-    const float e2 = (prod - (sum - bb)) + (c - bb);  // two-sum error
-    const float tail = e2 + fmaf(f, q_lo, e1);
-    const float h = rintf(sum);
+// Double-float splat setup from the float32 inputs: camera-frame centre,
+// projected centre f (x/z) + c split as integer part + remainder, and the
+// conic (inverse of J W Sigma W^T J^T + lowpass I).  The float32 recipe above
+// only decides the tile rectangle; the continuous quantities that alpha needs
+// are computed here to about 48 bits, because an elongated splat far from its
+// centre makes the quadratic form cancel by orders of magnitude.
+struct SplatFF {
+    float mxh, myh, mxl, myl;
+    ff A, B, C;
+    float kappa;
+};
+
+__device__ __forceinline__ void split_center(ff m, float* hi, float* lo) {
+    const float h = rintf(m.hi);
     *hi = h;
-    *lo = (sum - h) + tail;
+    *lo = __fadd_rn(__fsub_rn(m.hi, h), m.lo);  // m.hi - h is exact
+}
+
+__device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy, float muz,
+                                         float qw, float qx, float qy, float qz, float sx,
+                                         float sy, float sz, float lowpass, SplatFF& o) {
+    const float* W = cam.R_wc;
+    ff pc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        pc[i] = ff_add(ff_add(ff_add(two_prod(W[3 * i], mux), two_prod(W[3 * i + 1], muy)),
+                              two_prod(W[3 * i + 2], muz)),
+                       ff_from(cam.t_wc[i]));
+    const ff n2 = ff_add(ff_add(two_prod(qw, qw), two_prod(qx, qx)),
+                         ff_add(two_prod(qy, qy), two_prod(qz, qz)));
+    const ff qn = ff_sqrt(n2);
+    const ff w = ff_div(ff_from(qw), qn), x = ff_div(ff_from(qx), qn),
+             y = ff_div(ff_from(qy), qn), z = ff_div(ff_from(qz), qn);
+    const ff one = ff_from(1.f);
+    ff R[3][3];
+    R[0][0] = ff_sub(one, ff_scale(ff_add(ff_mul(y, y), ff_mul(z, z)), 2.f));
+    R[0][1] = ff_scale(ff_sub(ff_mul(x, y), ff_mul(w, z)), 2.f);
+    R[0][2] = ff_scale(ff_add(ff_mul(x, z), ff_mul(w, y)), 2.f);
+    R[1][0] = ff_scale(ff_add(ff_mul(x, y), ff_mul(w, z)), 2.f);
+    R[1][1] = ff_sub(one, ff_scale(ff_add(ff_mul(x, x), ff_mul(z, z)), 2.f));
+    R[1][2] = ff_scale(ff_sub(ff_mul(y, z), ff_mul(w, x)), 2.f);
+    R[2][0] = ff_scale(ff_sub(ff_mul(x, z), ff_mul(w, y)), 2.f);
+    R[2][1] = ff_scale(ff_add(ff_mul(y, z), ff_mul(w, x)), 2.f);
+    R[2][2] = ff_sub(one, ff_scale(ff_add(ff_mul(x, x), ff_mul(y, y)), 2.f));
+    const float s[3] = {sx, sy, sz};
+    ff M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = ff_mul_f(R[i][j], s[j]);
+    const ff iz = ff_div(one, pc[2]);
+    const ff xz = ff_mul(pc[0], iz), yz = ff_mul(pc[1], iz);
+    const ff J00 = ff_mul_f(iz, cam.fx), J11 = ff_mul_f(iz, cam.fy);
+    const ff J02 = ff_neg(ff_mul(J00, xz)), J12 = ff_neg(ff_mul(J11, yz));
+    // V = T M with T = J R_wc (2x3); cov = V V^T + lowpass I
+    ff T[2][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T[0][j] = ff_add(ff_mul_f(J00, W[j]), ff_mul_f(J02, W[6 + j]));
+        T[1][j] = ff_add(ff_mul_f(J11, W[3 + j]), ff_mul_f(J12, W[6 + j]));
+    }
+    ff V[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            V[i][j] = ff_add(ff_add(ff_mul(T[i][0], M[0][j]), ff_mul(T[i][1], M[1][j])),
+                             ff_mul(T[i][2], M[2][j]));
+    const ff lp = ff_from(lowpass);
+    const ff c00 = ff_add(ff_add(ff_add(ff_mul(V[0][0], V[0][0]), ff_mul(V[0][1], V[0][1])),
+                                 ff_mul(V[0][2], V[0][2])), lp);
+    const ff c11 = ff_add(ff_add(ff_add(ff_mul(V[1][0], V[1][0]), ff_mul(V[1][1], V[1][1])),
+                                 ff_mul(V[1][2], V[1][2])), lp);
+    const ff c01 = ff_add(ff_add(ff_mul(V[0][0], V[1][0]), ff_mul(V[0][1], V[1][1])),
+                          ff_mul(V[0][2], V[1][2]));
+    const ff det = ff_sub(ff_mul(c00, c11), ff_mul(c01, c01));
+    o.A = ff_div(c11, det);
+    o.B = ff_neg(ff_div(c01, det));
+    o.C = ff_div(c00, det);
+    split_center(ff_add(ff_mul_f(xz, cam.fx), ff_from(cam.cx)), &o.mxh, &o.mxl);
+    split_center(ff_add(ff_mul_f(yz, cam.fy), ff_from(cam.cy)), &o.myh, &o.myl);
+    // eigenvalue ratio of the conic: lmax^2 / det(conic)
+    const float a = o.A.hi, b = o.B.hi, c = o.C.hi;
+    const float lmax = 0.5f * (a + c) + sqrtf(0.25f * (a - c) * (a - c) + b * b);
+    const float detK = 1.f / ff_val(det);
+    o.kappa = lmax * lmax / fmaxf(detK, 1e-30f);
 }
 
 __global__ void __launch_bounds__(256)
@@ -173,14 +244,21 @@ __global__ void __launch_bounds__(256)
         zbits[t] = __float_as_uint(rc.pz);
 
         float o[REC_FLOATS];
-        compensated_center(rc.px, rc.pz, cam.fx, cam.cx, &o[R_MXH], &o[R_MXL]);
-        compensated_center(rc.py, rc.pz, cam.fy, cam.cy, &o[R_MYH], &o[R_MYL]);
+        SplatFF sf;
+        splat_ff(cam, mux, muy, muz, qw, qx, qy, qz, sx, sy, sz, lowpass, sf);
+        o[R_MXH] = sf.mxh;
+        o[R_MYH] = sf.myh;
+        o[R_MXL] = sf.mxl;
+        o[R_MYL] = sf.myl;
         o[R_OP] = __ldg(g.opacity + i);
         o[R_K] = __ldg(g.kfac + i);
-        const float idet = 1.f / rc.det;
-        o[R_CON + 0] = rc.c * idet;
-        o[R_CON + 1] = -rc.b * idet;
-        o[R_CON + 2] = rc.a * idet;
+        o[R_CON + 0] = sf.A.hi;
+        o[R_CON + 1] = sf.B.hi;
+        o[R_CON + 2] = sf.C.hi;
+        o[R_CLO + 0] = sf.A.lo;
+        o[R_CLO + 1] = sf.B.lo;
+        o[R_CLO + 2] = sf.C.lo;
+        o[R_FLAG] = sf.kappa > KAPPA_FF ? 1.f : 0.f;
 
         // colour from SH, viewing direction mu - C
         float dx = mux - cam.C[0], dy = muy - cam.C[1], dz = muz - cam.C[2];
@@ -216,8 +294,8 @@ __global__ void __launch_bounds__(256)
             for (int b = 0; b < 3; ++b) o[R_NW + a * 3 + b] = rc.R[a][b] * is[b];
         }
         o[R_Z] = rc.pz;
-        o[34] = 0.f;
-        o[35] = 0.f;
+        o[38] = 0.f;
+        o[39] = 0.f;
         float4* dst = reinterpret_cast<float4*>(rec + (size_t)t * REC_FLOATS);
 #pragma unroll
         for (int q = 0; q < REC_FLOATS / 4; ++q)
@@ -233,6 +311,8 @@ __global__ void init_kernel(CamTable tab, int n_cams, CamTable* __restrict__ dst
         hdr->status = 0;
         hdr->n_instances = 0;
         hdr->need = 0;
+        hdr->n_eval = 0;
+        hdr->n_blend = 0;
     }
 }
 

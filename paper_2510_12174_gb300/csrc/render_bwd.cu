@@ -306,6 +306,7 @@ struct PreBwdParams {
     const CamTable* tab;
     int n_cams;
     unigs_gaussians g;
+    const float* rec;
     const float* grec;
     const uint32_t* touched;
     unigs_param_grads out;
@@ -361,6 +362,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
             }
             g_op += gr[G_OP];
             g_k += gr[G_K];
+            const float* rec_conic = P.rec + t * REC_FLOATS + R_CON;
 
             // ---- colour -> SH and viewing direction
             {
@@ -409,17 +411,13 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
             for (int a = 0; a < 2; ++a)
                 for (int j = 0; j < 3; ++j)
                     U[a][j] = Tm[a][0] * Sig[0][j] + Tm[a][1] * Sig[1][j] + Tm[a][2] * Sig[2][j];
-            const float ca = U[0][0] * Tm[0][0] + U[0][1] * Tm[0][1] + U[0][2] * Tm[0][2] + P.lowpass;
-            const float cb = U[0][0] * Tm[1][0] + U[0][1] * Tm[1][1] + U[0][2] * Tm[1][2];
-            const float cc = U[1][0] * Tm[1][0] + U[1][1] * Tm[1][1] + U[1][2] * Tm[1][2] + P.lowpass;
-            const float det = ca * cc - cb * cb;
-            const float id2 = 1.f / (det * det);
+            // conic K = cov^-1: dL/dcov = -K G K with G = [[gA, gB/2], [gB/2, gC]]
+            // (no determinant subtraction, so near-diagonal covariances do not cancel)
+            const float KA = rec_conic[0], KB = rec_conic[1], KC = rec_conic[2];
             const float gA = gr[G_CA], gB = gr[G_CB], gC = gr[G_CC];
-            // conic (A,B,C) = (c, -b, a) / det
-            const float g_ca = (-cc * cc * gA + cb * cc * gB + (det - ca * cc) * gC) * id2;
-            const float g_cb = (2.f * cb * cc * gA + (-det - 2.f * cb * cb) * gB + 2.f * ca * cb * gC) * id2;
-            const float g_cc = ((det - ca * cc) * gA + ca * cb * gB - ca * ca * gC) * id2;
-            // cov = T Sigma T^T: G_cov symmetric with the off-diagonal halved
+            const float g_ca = -(KA * KA * gA + KA * KB * gB + KB * KB * gC);
+            const float g_cb = -(2.f * KA * KB * gA + (KA * KC + KB * KB) * gB + 2.f * KB * KC * gC);
+            const float g_cc = -(KB * KB * gA + KB * KC * gB + KC * KC * gC);
             const float Gc[2][2] = {{g_ca, 0.5f * g_cb}, {0.5f * g_cb, g_cc}};
             // dL/dSigma = T^T G T
             float gSig[3][3];
@@ -520,8 +518,12 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
 template <int NS, typename FT>
 static void launch_bwd_t(const BwdParams& P, int64_t n_tiles, cudaStream_t st) {
     const size_t smem = sizeof(BwdSmem<NS, FT>);
-    cudaFuncSetAttribute(render_bwd_kernel<NS, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    static bool attr_set = false;  // host-side, set once per instantiation
+    if (!attr_set) {
+        cudaFuncSetAttribute(render_bwd_kernel<NS, FT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
     render_bwd_kernel<NS, FT><<<(unsigned)n_tiles, 256, smem, st>>>(P);
 }
 
@@ -579,6 +581,7 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         Q.tab = ws_ptr<CamTable>(ws, p, OFF_CAM);
         Q.n_cams = p.n_cams;
         Q.g = g;
+        Q.rec = ws_ptr<float>(ws, p, OFF_REC);
         Q.grec = grec;
         Q.touched = ws_ptr<uint32_t>(ws, p, OFF_TOUCH);
         Q.out = grads;

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
 #pragma unroll
     for (int c = 0; c < NS; ++c) co[c] = 0.f;
     uint32_t last = 0;
+    uint32_t n_eval = 0, n_blend = 0;
     bool done = !inside;
     bool timed_out = false;
 
@@ -154,12 +155,14 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
                 const float* rc = &S.rec[buf][j][0];
                 float dx, dy, Gs;
                 const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                ++n_eval;
                 if (alpha < P.alpha_min) continue;
                 const float test_T = T * (1.f - alpha);
                 if (test_T < P.T_min) {
                     done = true;
                     continue;
                 }
+                ++n_blend;
                 const float w = alpha * T;
                 PairGeom G;
                 pair_geometry(rc, xt, yt, G);
@@ -187,6 +190,16 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         }
     }
     if (timed_out && (tid & 31) == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
+    // work counters: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
+        n_blend += __shfl_xor_sync(0xffffffffu, n_blend, o);
+    }
+    if ((tid & 31) == 0 && n_eval) {
+        atomicAdd(&P.hdr->n_eval, (unsigned long long)n_eval);
+        atomicAdd(&P.hdr->n_blend, (unsigned long long)n_blend);
+    }
     if (!inside) return;
     const int H = cam.height, W = cam.width;
     const int64_t HW = (int64_t)H * W;
@@ -213,8 +226,12 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
 template <int NS, typename FT>
 static void launch_fwd_t(const FwdParams& P, int64_t n_tiles, cudaStream_t st) {
     const size_t smem = sizeof(FwdSmem<NS, FT>);
-    cudaFuncSetAttribute(render_fwd_kernel<NS, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    static bool attr_set = false;  // host-side, set once per instantiation
+    if (!attr_set) {
+        cudaFuncSetAttribute(render_fwd_kernel<NS, FT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
     render_fwd_kernel<NS, FT><<<(unsigned)n_tiles, 256, smem, st>>>(P);
 }
 

@@ -14,21 +14,28 @@ constexpr int TILE_PIX = TILE * TILE;
 
 // ----------------------------------------------------------------------------
 // Per-(camera, Gaussian) forward record written by the preprocess and staged
-// into shared memory by the composite kernels (36 floats = 144 bytes, a
+// into shared memory by the composite kernels (40 floats = 160 bytes, a
 // multiple of 16 so a bulk copy can move it).
 //   [0..3]  projected centre split as integer part + remainder (x_hi, y_hi,
 //           x_lo, y_lo); m = hi + lo, hi an integer-valued float, |lo| <= 0.5
 //   [4]     opacity     [5] k (gradient factor)   [6..8] RGB
-//   [9..11] conic (A, B, C) of the inverse 2D covariance
+//   [9..11] conic (A, B, C) of the inverse 2D covariance (high words)
 //   [12..20] M_c = S^-1 R^T R_cw (camera ray -> local scaled), row-major
 //   [21..23] v_s = S^-1 R^T (C - mu)
 //   [24..32] N_w = R S^-1 (scaled-local normal -> world), row-major
-//   [33]    camera-frame z of the centre   [34..35] unused
+//   [33]    camera-frame z of the centre
+//   [34..36] low words of the conic (double-float A, B, C)
+//   [37]    1 when the splat is ill-conditioned (alpha evaluated in
+//           double-float), else 0      [38..39] unused
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_OP, R_K, R_RGB, R_CON = 9, R_MC = 12,
-    R_VS = 21, R_NW = 24, R_Z = 33, REC_FLOATS = 36
+    R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34, R_FLAG = 37, REC_FLOATS = 40
 };
+
+// Conic eigenvalue ratio above which alpha is evaluated in double-float: the
+// float32 quadratic form loses about log2(ratio) bits along the long axis.
+constexpr float KAPPA_FF = 64.f;
 
 // Per-(camera, Gaussian) intermediate gradient record (32 floats), filled by
 // atomics in the backward composite and consumed by the preprocess backward.
@@ -60,7 +67,9 @@ struct WsHeader {
     uint32_t status;       // unigs_status of the first device-side error
     uint32_t n_instances;  // instances emitted (valid when not overflowed)
     unsigned long long need;  // instances required (capacity errors)
-    uint32_t pad[60];
+    unsigned long long n_eval;   // (pixel, Gaussian) pairs whose alpha the forward evaluated
+    unsigned long long n_blend;  // pairs the forward blended (alpha >= alpha_min, not stopped)
+    uint32_t pad[56];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 

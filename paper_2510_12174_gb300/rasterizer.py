@@ -236,6 +236,13 @@ class Renderer:
         s = abi.unigs_status_poll(self.plan, self.ws.data_ptr(), d, self._stream())
         return s, int(d.value)
 
+    def stats(self):
+        """(pairs evaluated, pairs blended) by the last forward."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        abi.check(abi.unigs_stats_poll(self.plan, self.ws.data_ptr(), a, b, self._stream()),
+                  "unigs_stats_poll")
+        return int(a.value), int(b.value)
+
     def launches_per_step(self) -> int:
         return abi.unigs_launches_per_step(self.plan)
 

@@ -210,9 +210,12 @@ def test_autograd_function_matches_direct_backward():
     r2 = rz.Renderer(rz.DeviceScene.from_scene(sc), cams)
     o2 = r2.forward()
     g2 = r2.backward(o2, up)
+    # the two runs differ only in the order of the float32 atomic additions
     for k, t in zip(("mean", "quat", "scale", "opacity", "kfac", "sh", "sem"), ds.tensors()):
         a, b = t.grad.float(), g2[k]
-        assert torch.allclose(a, b, rtol=1e-3, atol=1e-5 * float(b.abs().max()) + 1e-12), k
+        rms = float(b.pow(2).mean().sqrt())
+        rel = ((a - b).abs() / torch.clamp(b.abs(), min=1e-2 * rms + 1e-30)).max().item()
+        assert rel < 1e-3, (k, rel)
 
 
 @pytest.mark.parametrize("n", [1_000_000])
