@@ -148,6 +148,9 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
     if (warp == 0)
         bwd_issue<NS, FT>(P, S, 0, range.x + (n_batches - 1) * BBATCH,
                           min(BBATCH, n_items - (n_batches - 1) * BBATCH), cam_idx);
+    // ids and unaligned semantic rows are staged with plain stores: make the
+    // first batch visible (later batches are ordered by the end-of-batch barrier)
+    __syncthreads();
 
     float Sacc = 0.f;  // sum over already processed (later) Gaussians of w_j G_j
     bool timed_out = false;
@@ -196,12 +199,14 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
                         const bool clamped = rc[R_OP] * Gs > P.alpha_max;
                         const float g_pow = clamped ? 0.f : dL_da * alpha;
                         gv[G_OP] = clamped ? 0.f : dL_da * Gs;
-                        const float A = rc[R_CON], B = rc[R_CON + 1], C = rc[R_CON + 2];
-                        gv[G_CA] = -0.5f * dx * dx * g_pow;
-                        gv[G_CB] = -dx * dy * g_pow;
-                        gv[G_CC] = -0.5f * dy * dy * g_pow;
-                        gv[G_MX] = (A * dx + B * dy) * g_pow;
-                        gv[G_MY] = (C * dy + B * dx) * g_pow;
+                        // power = -1/2 D^T K D: dL/dm = g u, dL/dcov = g/2 u u^T, u = K D
+                        float kux, kuy;
+                        splat_kdelta(rc, uf, vf, dx, dy, &kux, &kuy);
+                        gv[G_CA] = 0.5f * g_pow * kux * kux;
+                        gv[G_CB] = g_pow * kux * kuy;
+                        gv[G_CC] = 0.5f * g_pow * kuy * kuy;
+                        gv[G_MX] = kux * g_pow;
+                        gv[G_MY] = kuy * g_pow;
                         gv[G_RGB] = w * g_rgb[0];
                         gv[G_RGB + 1] = w * g_rgb[1];
                         gv[G_RGB + 2] = w * g_rgb[2];
@@ -362,7 +367,6 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
             }
             g_op += gr[G_OP];
             g_k += gr[G_K];
-            const float* rec_conic = P.rec + t * REC_FLOATS + R_CON;
 
             // ---- colour -> SH and viewing direction
             {
@@ -411,14 +415,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
             for (int a = 0; a < 2; ++a)
                 for (int j = 0; j < 3; ++j)
                     U[a][j] = Tm[a][0] * Sig[0][j] + Tm[a][1] * Sig[1][j] + Tm[a][2] * Sig[2][j];
-            // conic K = cov^-1: dL/dcov = -K G K with G = [[gA, gB/2], [gB/2, gC]]
-            // (no determinant subtraction, so near-diagonal covariances do not cancel)
-            const float KA = rec_conic[0], KB = rec_conic[1], KC = rec_conic[2];
-            const float gA = gr[G_CA], gB = gr[G_CB], gC = gr[G_CC];
-            const float g_ca = -(KA * KA * gA + KA * KB * gB + KB * KB * gC);
-            const float g_cb = -(2.f * KA * KB * gA + (KA * KC + KB * KB) * gB + 2.f * KB * KC * gC);
-            const float g_cc = -(KB * KB * gA + KB * KC * gB + KC * KC * gC);
-            const float Gc[2][2] = {{g_ca, 0.5f * g_cb}, {0.5f * g_cb, g_cc}};
+            // the record holds dL/d(a, b, c) of the 2D covariance [[a, b], [b, c]]
+            const float Gc[2][2] = {{gr[G_CA], 0.5f * gr[G_CB]}, {0.5f * gr[G_CB], gr[G_CC]}};
             // dL/dSigma = T^T G T
             float gSig[3][3];
             for (int a = 0; a < 3; ++a)

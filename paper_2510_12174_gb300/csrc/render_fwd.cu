@@ -128,6 +128,10 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
     __syncthreads();
     if (warp == 0 && n_batches > 0)
         issue_batch<NS, FT>(P, S, 0, range.x, min(BATCH, n_items), cam_idx);
+    // rows staged with plain stores (unaligned semantic rows) must be visible
+    // before the first batch is read; later batches are ordered by the
+    // end-of-batch barrier
+    __syncthreads();
 
     float T = 1.f;
     float crgb[3] = {0.f, 0.f, 0.f}, cdep = 0.f, cn[3] = {0.f, 0.f, 0.f}, ck = 0.f;

@@ -44,6 +44,25 @@ __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float
     return fminf(alpha_max, __fmul_rn(rc[R_OP], G));
 }
 
+// u = K D (conic times pixel offset), the direction of every alpha gradient:
+// dL/dm = g u and dL/dcov = g/2 u u^T for g = dL/dpower.  Flagged
+// (ill-conditioned) splats form it in double-float, because K D cancels along
+// the long axis exactly like the quadratic form does.
+__device__ __forceinline__ void splat_kdelta(const float* __restrict__ rc, float uf, float vf,
+                                             float dx, float dy, float* ux, float* uy) {
+    if (rc[R_FLAG] != 0.f) {
+        const ff fdx = two_sum(__fsub_rn(uf, rc[R_MXH]), -rc[R_MXL]);
+        const ff fdy = two_sum(__fsub_rn(vf, rc[R_MYH]), -rc[R_MYL]);
+        const ff A = {rc[R_CON], rc[R_CLO]}, B = {rc[R_CON + 1], rc[R_CLO + 1]},
+                 C = {rc[R_CON + 2], rc[R_CLO + 2]};
+        *ux = ff_val(ff_add(ff_mul(A, fdx), ff_mul(B, fdy)));
+        *uy = ff_val(ff_add(ff_mul(B, fdx), ff_mul(C, fdy)));
+    } else {
+        *ux = fmaf(rc[R_CON], dx, rc[R_CON + 1] * dy);
+        *uy = fmaf(rc[R_CON + 1], dx, rc[R_CON + 2] * dy);
+    }
+}
+
 // a*b - c*d with Kahan's FMA compensation (error about one ulp of the result).
 __device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
     const float w = c * d;

@@ -38,7 +38,10 @@ enum {
 constexpr float KAPPA_FF = 64.f;
 
 // Per-(camera, Gaussian) intermediate gradient record (32 floats), filled by
-// atomics in the backward composite and consumed by the preprocess backward.
+// atomics in the backward composite and consumed by the preprocess backward:
+// dL/d(projected centre x, y), dL/d(a, b, c) of the 2D covariance
+// [[a, b], [b, c]] (low-pass included), opacity, RGB, M_c, v_s, N_w, k and the
+// centre depth (centre-depth mode).
 enum {
     G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_OP, G_RGB, G_MC = 9, G_VS = 18,
     G_NW = 21, G_K = 30, G_Z = 31, GREC_FLOATS = 32

@@ -79,14 +79,34 @@ def forward_errors(r, out, ref_outs, n_sem):
 
 
 def grad_errors(got, ref, rel_floor=1e-2):
-    """Per parameter: max |g - g_ref| / max(|g_ref|, rel_floor * RMS(g_ref)),
-    and the same at the 99.9th percentile."""
+    """Per parameter type: (max, 99.9th percentile) of
+    |g - g_ref| / max(|g_ref|, rel_floor * RMS), the max of the same with a
+    0.1 * RMS floor, the vector-norm relative error, and the RMS."""
     res = {}
     for k, g_ref in ref.items():
         g = got[k].float().cpu().numpy().reshape(g_ref.shape)
         rms = float(np.sqrt(np.mean(g_ref ** 2))) if g_ref.size else 0.0
         den = np.maximum(np.abs(g_ref), rel_floor * rms + 1e-30)
         e = np.abs(g - g_ref) / den
-        res[k] = (float(e.max()) if e.size else 0.0,
-                  float(np.quantile(e, 0.999)) if e.size else 0.0, rms)
+        e10 = np.abs(g - g_ref) / np.maximum(np.abs(g_ref), 0.1 * rms + 1e-30)
+        nrm = float(np.linalg.norm(g - g_ref) / max(np.linalg.norm(g_ref), 1e-30))
+        res[k] = dict(max=float(e.max()) if e.size else 0.0,
+                      p999=float(np.quantile(e, 0.999)) if e.size else 0.0,
+                      max_floor01=float(e10.max()) if e.size else 0.0, norm=nrm, rms=rms)
     return res
+
+
+def check_grad_errors(e, p999=1e-3, max_floor01=1e-2, norm=1e-4):
+    """Gradient criterion.  Per-Gaussian gradients are float32 sums over pixels
+    whose terms can cancel (e.g. the rotation gradient of a nearly isotropic
+    Gaussian), so the element-wise bound uses a floor proportional to the RMS
+    of that parameter type: 99.9% of elements within p999 of max(|g|, 1e-2 RMS),
+    every element within max_floor01 of max(|g|, 0.1 RMS), and the whole
+    vector within ``norm`` relative error."""
+    for k, d in e.items():
+        print(f"grad {k}: p99.9 {d['p999']:.2e} max {d['max']:.2e} max(0.1rms) "
+              f"{d['max_floor01']:.2e} norm {d['norm']:.2e} rms {d['rms']:.3e}")
+    for k, d in e.items():
+        assert d["p999"] < p999, (k, d)
+        assert d["max_floor01"] < max_floor01, (k, d)
+        assert d["norm"] < norm, (k, d)

@@ -15,8 +15,8 @@ from paper_2510_12174_gb300 import abi
 from paper_2510_12174_gb300 import rasterizer as rz
 from paper_2510_12174_gb300 import scenes
 
-from gpu_helpers import (TOL_ABS, TOL_REL, dilate, flat_upstream, forward_errors, grad_errors,
-                         masked_upstream)
+from gpu_helpers import (TOL_ABS, TOL_REL, check_grad_errors, dilate, flat_upstream,
+                         forward_errors, grad_errors, masked_upstream)
 
 pytestmark = pytest.mark.gpu
 
@@ -153,21 +153,21 @@ def _grad_case(sc, cams, with_nd=False, seed=21):
 
 def test_backward_parity():
     sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=8, seed=12)
-    e = _grad_case(sc, cams)
-    for k, (mx, q999, rms) in e.items():
-        print(f"grad {k}: max {mx:.2e} p99.9 {q999:.2e} rms {rms:.3e}")
-    for k, (mx, q999, rms) in e.items():
-        assert q999 < 1e-3, k
-        assert mx < 1e-2, k
+    check_grad_errors(_grad_case(sc, cams))
 
 
 def test_backward_parity_two_cameras_with_depth_normal():
+    """Includes Alg. 3: the depth gradient then carries the normal-from-depth
+    term, whose float32 error grows with f/step (see the A6 note), so the
+    element-wise bound is 3x looser."""
     sc, cams = scenes.small_room(n=5000, width=60, height=44, n_sem=16, seed=13, n_cams=2)
-    e = _grad_case(sc, cams, with_nd=True)
-    for k, (mx, q999, rms) in e.items():
-        print(f"grad+nd {k}: max {mx:.2e} p99.9 {q999:.2e} rms {rms:.3e}")
-    for k, (mx, q999, rms) in e.items():
-        assert q999 < 1e-2, k
+    check_grad_errors(_grad_case(sc, cams, with_nd=True), p999=3e-3, max_floor01=3e-2,
+                      norm=3e-4)
+
+
+def test_backward_parity_bf16_features():
+    sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=16, seed=17, feat_bf16=True)
+    check_grad_errors(_grad_case(sc, cams))
 
 
 def test_capacity_overflow_reports_and_recovers():
@@ -261,3 +261,76 @@ def test_full_size_sampled_pixels(n):
     assert n_amb < 30
     assert worst["rgb"] < TOL_ABS and worst["normal_g"] < TOL_ABS and worst["kmap"] < TOL_ABS
     assert worst["depth"] < TOL_REL and worst["logits"] < 10 * TOL_REL
+
+
+def test_full_size_finite_differences_64_params():
+    """1M Gaussians at 1280x720, 64 logits: the analytic gradient against GPU
+    central differences of L = sum_c <output_c, upstream_c> on 64 parameters
+    drawn from Gaussians that contribute, stratified over mu, q, s, opacity,
+    SH, logits and k.  The forward is deterministic, so pixels the
+    perturbation does not reach cancel exactly in L(+h) - L(-h) (summed in
+    float64); a pair of steps h and h/2 that disagree marks a discrete change
+    (a tile rectangle, the alpha threshold) and the sample is redrawn."""
+    sc, cams = scenes.config3()
+    ds = rz.DeviceScene.from_scene(sc)
+    r = rz.Renderer(ds, cams)
+    up = flat_upstream(scenes.upstream_grads(cams, sc.n_sem, seed=31),
+                       keys=("rgb", "depth", "normal_g", "kmap", "logits"))
+    out = r.forward(normal_d=False)
+    grads = r.backward(out, up)
+    torch.cuda.synchronize()
+    keys, vals, _ = r.sorted_instances()
+    nc = out["n_contrib"]
+    del out
+
+    def loss():
+        o = r.forward(normal_d=False)
+        return sum(float((o[k].double() * up[k].double()).sum()) for k in up)
+
+    rng = np.random.default_rng(3)
+    cand = np.unique(vals)
+    names = ["mean", "quat", "scale", "opacity", "sh", "sem", "kfac"]
+    checked = {n: 0 for n in names}
+    worst = 0.0
+    tries = 0
+    while min(checked.values()) < 9 and tries < 400:
+        tries += 1
+        name = names[tries % len(names)]
+        if checked[name] >= 10:
+            continue
+        g = int(rng.choice(cand))
+        t = getattr(ds, name)
+        if t.dim() == 1:
+            idx = (g,)
+        elif name in ("mean", "quat", "scale"):
+            idx = (int(rng.integers(0, t.shape[0])), g)
+        elif name == "sh":
+            idx = (g, int(rng.integers(0, t.shape[1])), int(rng.integers(0, 3)))
+        else:
+            idx = (g, int(rng.integers(0, t.shape[1])))
+        an = float(grads[name][idx])
+        x0 = float(t[idx])
+        def fd(h):
+            t[idx] = x0 + h
+            lp = loss()
+            t[idx] = x0 - h
+            lm = loss()
+            t[idx] = x0
+            return (lp - lm) / (2 * h)
+        if name == "mean":
+            h = 2e-4
+        elif name in ("sem", "kfac", "sh"):
+            h = 5e-2  # the outputs are (piecewise) linear in these: a large step
+        else:
+            h = 2e-3 * max(abs(x0), 1e-2)
+        f1, f2 = fd(h), fd(h / 2)
+        if abs(f1 - f2) > 2e-2 * max(abs(f1), abs(f2), 1e-3):
+            continue  # discrete change inside the stencil
+        if abs(f2) < 1e-3 and abs(an) < 1e-3:
+            continue  # no signal to compare
+        rel = abs(an - f2) / max(abs(f2), 1e-2)
+        worst = max(worst, rel)
+        checked[name] += 1
+        assert rel < 2e-2, (name, idx, an, f1, f2)
+    print("FD checked", checked, "worst rel", worst)
+    assert sum(checked.values()) >= 64
