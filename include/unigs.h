@@ -254,6 +254,33 @@ int32_t unigs_launches_per_step(const unigs_plan* plan);
 
 const char* unigs_status_string(unigs_status s);
 
+/* Allocation-free sort (the paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory where they call, e.g. code with a
+ * memory budget fixed at start-up, a plugin host that owns every allocation,
+ * or a real-time loop in which a cudaMalloc may not run).
+ *
+ * Stable LSD radix sort of n (key, value) pairs by the low key_bits bits of
+ * the key - the sort unigs_bin_sort runs on the tile|depth keys - but with its
+ * scratch memory (one ping-pong buffer, digit histograms, scan partials, a
+ * status block) in a static device array of the library rather than in a
+ * caller workspace.  The caller passes device inputs and outputs only; the
+ * outputs must not overlap the inputs.  Sorted order: ascending key, ties in
+ * input order.
+ *
+ * Limits and behaviour: n <= UNIGS_STATIC_SORT_MAX_PAIRS (2^20); larger n,
+ * key_bits outside 1..64, or NULL / aliased buffers return
+ * UNIGS_ERR_INVALID_ARG before anything runs.  The static array (about
+ * 12.5 MB) is held by every GPU that loads the library until the process
+ * exits.  The first call on a device (with that device current, and the
+ * stream on that device) looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the one array and
+ * overwrites it: calls that overlap on the GPU (other streams, other host
+ * threads) race.  Asynchronous on the stream; calls no allocator. */
+#define UNIGS_STATIC_SORT_MAX_PAIRS (1 << 20)
+unigs_status unigs_sort_pairs_static(const unsigned long long* keys_in, const uint32_t* vals_in,
+                                     int64_t n, int32_t key_bits, unsigned long long* keys_out,
+                                     uint32_t* vals_out, unigs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

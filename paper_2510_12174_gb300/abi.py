@@ -18,6 +18,7 @@ UNIGS_MAX_CAMS = 64
 UNIGS_TILE = 16
 UNIGS_MAX_SEM = 64
 UNIGS_FLAG_CENTER_DEPTH = 1
+UNIGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 
 UNIGS_OK = 0
 UNIGS_ERR_INVALID_ARG = 1
@@ -99,6 +100,8 @@ _SIGS = [
                                    POINTER(c_int64), c_void_p]),
     ("unigs_launches_per_step", c_int32, [POINTER(unigs_plan)]),
     ("unigs_status_string", c_char_p, [c_int32]),
+    ("unigs_sort_pairs_static", c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p,
+                                          c_void_p, c_void_p]),
 ]
 
 
@@ -190,6 +193,14 @@ def unigs_status_poll(plan, ws, detail, stream) -> int:
 def unigs_stats_poll(plan, ws, n_eval, n_blend, stream) -> int:
     return lib().unigs_stats_poll(ctypes.byref(plan), ws, ctypes.byref(n_eval),
                                   ctypes.byref(n_blend), stream)
+
+
+def unigs_sort_pairs_static(keys_in, vals_in, n, key_bits, keys_out, vals_out, stream) -> int:
+    """Allocation-free stable radix sort of (u64 key, u32 value) pairs by the
+    low ``key_bits`` bits; device pointers; scratch is the library's static
+    array (see include/unigs.h)."""
+    return lib().unigs_sort_pairs_static(keys_in, vals_in, n, key_bits, keys_out, vals_out,
+                                         stream)
 
 
 def unigs_launches_per_step(plan) -> int:

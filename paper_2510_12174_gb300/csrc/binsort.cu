@@ -249,6 +249,15 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long long* kout,
+               uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
+               int shift, int nb, cudaStream_t st) {
+    radix_hist_kernel<<<nb, 256, 0, st>>>(kin, hdr, shift, nb, hist);
+    int launches = 1 + scan_u32(hist, (int64_t)nb * 256, scan_tmp, hist, nullptr, st);
+    radix_scatter_kernel<<<nb, 256, 0, st>>>(kin, vin, kout, vout, hist, hdr, shift, nb);
+    return launches + 1;
+}
+
 int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
     const int64_t total = p.n * (int64_t)p.n_cams;
     WsHeader* hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);

@@ -20,6 +20,14 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_outputs& fwd, const unigs_grad_outputs& go,
                       const unigs_param_grads& grads, cudaStream_t st);
 
+// One stable 8-bit LSD radix pass over the n = hdr->n_instances pairs (n read
+// on the device; 0 when hdr->status reports a capacity overflow): per-block
+// digit histograms, their exclusive scan, stable scatter.  nb blocks of
+// SORT_ITEMS pairs; hist holds 256 * nb counters, scan_tmp the scan partials.
+int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long long* kout,
+               uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
+               int shift, int nb, cudaStream_t st);
+
 // Index of the buffer (0/1) that holds the sorted keys/values after the sort.
 inline int sorted_buffer(const unigs_plan& p) { return p.sort_passes & 1; }
 
