@@ -324,8 +324,11 @@ def test_full_size_finite_differences_64_params():
         else:
             h = 2e-3 * max(abs(x0), 1e-2)
         f1, f2 = fd(h), fd(h / 2)
-        if abs(f1 - f2) > 2e-2 * max(abs(f1), abs(f2), 1e-3):
-            continue  # discrete change inside the stencil
+        # an alpha-threshold, termination or tile-rectangle crossing inside the
+        # stencil adds jump / 2h to the difference quotient; such samples show
+        # as disagreement between the two steps (float32 noise here is ~2e-4)
+        if abs(f1 - f2) > 3e-3 * max(abs(f1), abs(f2), 1e-3):
+            continue
         if abs(f2) < 1e-3 and abs(an) < 1e-3:
             continue  # no signal to compare
         rel = abs(an - f2) / max(abs(f2), 1e-2)
