@@ -38,6 +38,25 @@ The recipe, per (camera, Gaussian); (+) and (*) are float32 add and multiply:
         (same for y with TY); cull if the rectangle is empty
   key  = (global tile id << 32) | float32 bits of p_c.z
 
+Opacity-aware tile test.  Alg. 2 skips a Gaussian at a pixel where its alpha
+is below 1/255, so a (tile, Gaussian) pair only has to be listed when alpha
+can reach 1/255 somewhere in the tile.  With the float32 conic
+kA = c/det, kB = -(b/det), kC = a/det and q(D) = D^T K D, alpha >= 1/255
+needs q <= 2 ln(255 opacity).  The recipe bounds the logarithm from above
+without a transcendental: 255*op = m 2^e with m in [1, 2) (exact), and
+ln(255 op) <= e*LN2 + (m - 1) (ln m <= m - 1), so
+  qlim = (2 (e*LN2 + (m - 1))) * 1.01 + 0.05      (LN2 = float32(ln 2), margin
+                                                  for float32 evaluation)
+and a rectangle tile is kept iff the minimum of q over the tile's pixel-centre
+square [16tx, 16tx+15] x [16ty, 16ty+15] is <= qlim.  That minimum is 0 when
+the centre lies in the square, else the least of the four edge minima: on a
+vertical edge x = xe, dx = xe - m_x, dy = clamp(-(kB*dx)/kC, Y0 - m_y, Y1 - m_y)
+(and symmetrically on horizontal edges), q = ((kA*dx)*dx + ((2*kB)*dx)*dy)
++ (kC*dy)*dy.  Strongly elongated splats, (a + c)^2 > 4096 det, keep every
+tile of their rectangle (float32 cannot resolve their minimum reliably).  The
+culled pairs have alpha < 1/255 at every pixel of the tile, so the rendered
+result is the one the full rectangle gives.
+
 Within a tile the list is ordered by (depth bits, Gaussian index): a stable
 sort by the 64-bit key of the instances emitted in (camera, Gaussian, tile
 row-major) order.
@@ -57,6 +76,40 @@ def _rect_axis(m, r, n_tiles):
     lo = np.fmin(np.fmax(lo, f32(0)), nt)
     hi = np.fmin(np.fmax(hi, f32(0)), nt)
     return lo.astype(np.int64), hi.astype(np.int64)
+
+
+LN2_F32 = f32(0.6931471805599453)
+
+
+def tile_keep(pr, g, tx, ty):
+    """Opacity-aware tile test for Gaussian indices ``g`` and tile coordinates
+    (arrays of equal length), float32 recipe of the module docstring."""
+    mx, my = pr["mean2d"][0][g], pr["mean2d"][1][g]
+    kA, kB, kC = pr["conic32"][0][g], pr["conic32"][1][g], pr["conic32"][2][g]
+    qlim = pr["qlim"][g]
+    X0 = (tx * TILE).astype(f32)
+    X1 = (tx * TILE + (TILE - 1)).astype(f32)
+    Y0 = (ty * TILE).astype(f32)
+    Y1 = (ty * TILE + (TILE - 1)).astype(f32)
+    two = f32(2)
+    with np.errstate(all="ignore"):
+        def qf(dx, dy):
+            return ((kA * dx) * dx + ((two * kB) * dx) * dy) + (kC * dy) * dy
+
+        def vert(xe):
+            dx = xe - mx
+            dy = np.fmin(np.fmax(-(kB * dx) / kC, Y0 - my), Y1 - my)
+            return qf(dx, dy)
+
+        def horiz(ye):
+            dy = ye - my
+            dx = np.fmin(np.fmax(-(kB * dy) / kA, X0 - mx), X1 - mx)
+            return qf(dx, dy)
+
+        qmin = np.fmin(np.fmin(vert(X0), vert(X1)), np.fmin(horiz(Y0), horiz(Y1)))
+        inside = (X0 <= mx) & (mx <= X1) & (Y0 <= my) & (my <= Y1)
+        qmin = np.where(inside, f32(0), qmin)
+    return pr["no_cull"][g] | (qmin <= qlim)
 
 
 def project_fp32(scene, cam, tile: int = TILE) -> dict:
@@ -118,12 +171,46 @@ def project_fp32(scene, cam, tile: int = TILE) -> dict:
         x0, x1 = _rect_axis(mx, r, TX)
         y0, y1 = _rect_axis(my, r, TY)
         valid = in_front & qok & det_ok & (x1 > x0) & (y1 > y0)
-        touched = np.where(valid, (x1 - x0) * (y1 - y0), 0)
+        # opacity-aware tile test (module docstring)
+        kA = c / det
+        kB = -(b / det)
+        kC = a / det
+        ac = a + c
+        no_cull = (ac * ac) > (f32(4096) * det)
+        y = f32(255) * scene.opacity.astype(f32)
+        mant, ex = np.frexp(y)             # y = mant * 2^ex, mant in [0.5, 1)
+        m = (mant * two).astype(f32)       # exact
+        e = (ex - 1).astype(f32)
+        lnb = e * LN2_F32 + (m - one)
+        qlim = (two * lnb) * f32(1.01) + f32(0.05)
     zbits = pz.astype(f32).view(np.uint32)
-    return dict(p_c=np.stack(p), z=pz, zbits=zbits, cov2d=np.stack([a, b, c]),
-                det=det, radius=r, mean2d=np.stack([mx, my]),
-                rect=np.stack([x0, x1, y0, y1]), touched=touched.astype(np.int64),
-                valid=valid, tiles_x=TX, tiles_y=TY)
+    pr = dict(p_c=np.stack(p), z=pz, zbits=zbits, cov2d=np.stack([a, b, c]),
+              det=det, radius=r, mean2d=np.stack([mx, my]),
+              rect=np.stack([x0, x1, y0, y1]), valid=valid, tiles_x=TX, tiles_y=TY,
+              conic32=np.stack([kA, kB, kC]), qlim=qlim, no_cull=no_cull)
+    # tiles kept per Gaussian
+    touched = np.zeros(pz.shape[0], dtype=np.int64)
+    idx = np.nonzero(valid)[0]
+    if idx.size:
+        gg, tx, ty = _rect_tiles(pr, idx)
+        keep = tile_keep(pr, gg, tx, ty)
+        touched = np.bincount(gg[keep], minlength=pz.shape[0]).astype(np.int64)
+    pr["touched"] = touched
+    return pr
+
+
+def _rect_tiles(pr, idx):
+    """All (Gaussian, tx, ty) of the rectangles of Gaussians ``idx``, in
+    (Gaussian, row-major tile) order."""
+    x0, x1, y0, y1 = [v.astype(np.int64) for v in pr["rect"][:, idx]]
+    wdt = x1 - x0
+    cnt = wdt * (y1 - y0)
+    rep = np.repeat(np.arange(idx.size), cnt)
+    first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    local = np.arange(rep.size) - first[rep]
+    ty = y0[rep] + local // wdt[rep]
+    tx = x0[rep] + local % wdt[rep]
+    return idx[rep], tx, ty
 
 
 def bin_cameras(scene, cams) -> dict:
@@ -144,6 +231,9 @@ def bin_cameras(scene, cams) -> dict:
         TX = pr["tiles_x"]
         for g, a0, a1, b0, b1 in zip(idx, x0, x1, y0, y1):
             ty, tx = np.meshgrid(np.arange(b0, b1), np.arange(a0, a1), indexing="ij")
+            ty, tx = ty.ravel(), tx.ravel()
+            keep = tile_keep(pr, np.full(ty.size, g), tx, ty)
+            ty, tx = ty[keep], tx[keep]
             tiles = (tile_off[k] + ty * TX + tx).ravel().astype(np.uint64)
             keys_l.append((tiles << np.uint64(32)) | np.uint64(pr["zbits"][g]))
             vals_l.append(np.full(tiles.size, g, dtype=np.uint32))
@@ -175,17 +265,12 @@ def bin_cameras_fast(scene, cams) -> dict:
         idx = np.nonzero(pr["valid"])[0]
         if idx.size == 0:
             continue
-        x0, x1, y0, y1 = [v.astype(np.int64) for v in pr["rect"][:, idx]]
-        wdt = x1 - x0
-        cnt = wdt * (y1 - y0)
-        rep = np.repeat(np.arange(idx.size), cnt)
-        first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
-        local = np.arange(rep.size) - first[rep]
-        ty = y0[rep] + local // wdt[rep]
-        tx = x0[rep] + local % wdt[rep]
+        gg, tx, ty = _rect_tiles(pr, idx)
+        keep = tile_keep(pr, gg, tx, ty)
+        gg, tx, ty = gg[keep], tx[keep], ty[keep]
         tiles = (tile_off[k] + ty * pr["tiles_x"] + tx).astype(np.uint64)
-        keys_l.append((tiles << np.uint64(32)) | pr["zbits"][idx][rep].astype(np.uint64))
-        vals_l.append(idx[rep].astype(np.uint32))
+        keys_l.append((tiles << np.uint64(32)) | pr["zbits"][gg].astype(np.uint64))
+        vals_l.append(gg.astype(np.uint32))
     keys = np.concatenate(keys_l) if keys_l else np.zeros(0, np.uint64)
     vals = np.concatenate(vals_l) if vals_l else np.zeros(0, np.uint32)
     order = np.argsort(keys, kind="stable")

@@ -301,13 +301,39 @@ def test_fp32_recipe_tracks_fp64_projection():
     assert np.all(3 * np.sqrt(cov[:, 2]) <= r + 1e-6)
 
 
+def _keep_scalar(pr, g, tx, ty):
+    """The opacity-aware tile test written out with float32 scalars."""
+    f = np.float32
+    if pr["no_cull"][g]:
+        return True
+    mx, my = f(pr["mean2d"][0][g]), f(pr["mean2d"][1][g])
+    kA, kB, kC = (f(pr["conic32"][i][g]) for i in range(3))
+    X0, X1, Y0, Y1 = f(16 * tx), f(16 * tx + 15), f(16 * ty), f(16 * ty + 15)
+    if X0 <= mx <= X1 and Y0 <= my <= Y1:
+        return True
+    best = None
+    for xe in (X0, X1):
+        dx = f(xe - mx)
+        dy = min(max(f(f(-(f(kB * dx))) / kC), f(Y0 - my)), f(Y1 - my))
+        q = f(f(f(f(kA * dx) * dx) + f(f(f(f(2) * kB) * dx) * dy)) + f(f(kC * dy) * dy))
+        best = q if best is None else min(best, q)
+    for ye in (Y0, Y1):
+        dy = f(ye - my)
+        dx = min(max(f(f(-(f(kB * dy))) / kA), f(X0 - mx)), f(X1 - mx))
+        q = f(f(f(f(kA * dx) * dx) + f(f(f(f(2) * kB) * dx) * dy)) + f(f(kC * dy) * dy))
+        best = min(best, q)
+    return bool(best <= pr["qlim"][g])
+
+
 def test_binning_matches_brute_force_rect_enumeration():
     sc, cams = scenes.small_room(n=600, n_cams=2, seed=9)
     b1 = ob.bin_cameras(sc, cams)
     b2 = ob.bin_cameras_fast(sc, cams)
     assert np.array_equal(b1["keys"], b2["keys"]) and np.array_equal(b1["vals"], b2["vals"])
     assert np.array_equal(b1["ranges"], b2["ranges"])
-    # brute force: per tile, all Gaussians whose rectangle contains it, by (zbits, idx)
+    # brute force: per tile, every Gaussian whose rectangle contains it and that
+    # passes the tile test, ordered by (depth bits, index)
+    n_culled = 0
     for k, cam in enumerate(cams):
         pr = b1["projs"][k]
         TX, TY = pr["tiles_x"], pr["tiles_y"]
@@ -315,10 +341,40 @@ def test_binning_matches_brute_force_rect_enumeration():
         for t in range(TX * TY):
             ty, tx = divmod(t, TX)
             inside = pr["valid"] & (x0 <= tx) & (tx < x1) & (y0 <= ty) & (ty < y1)
-            ids = np.nonzero(inside)[0]
-            ids = ids[np.lexsort((ids, pr["zbits"][ids]))]
+            ids = [g for g in np.nonzero(inside)[0] if _keep_scalar(pr, g, tx, ty)]
+            n_culled += int(inside.sum()) - len(ids)
+            ids = np.array(ids, dtype=np.int64)
+            ids = ids[np.lexsort((ids, pr["zbits"][ids]))] if ids.size else ids
             s0, s1 = b1["ranges"][b1["tile_offset"][k] + t]
             assert np.array_equal(b1["vals"][s0:s1], ids)
+    assert n_culled > 0
+
+
+def test_tile_culling_is_conservative():
+    """Every (tile, Gaussian) pair the opacity-aware test drops has float64
+    alpha < 1/255 at every pixel of the tile (so Alg. 2 would skip it)."""
+    sc, cams = scenes.small_room(n=4000, width=90, height=70, seed=19)
+    cam = cams[0]
+    pr = ob.project_fp32(sc, cam)
+    prep = orr.preprocess(orr.Params.from_scene(sc), cam)
+    idx = np.nonzero(pr["valid"])[0]
+    gg, tx, ty = ob._rect_tiles(pr, idx)
+    keep = ob.tile_keep(pr, gg, tx, ty)
+    drop = np.nonzero(~keep)[0]
+    assert 0.3 < drop.size / keep.size
+    m = prep.mean2d.detach().numpy()
+    con = prep.conic.detach().numpy()
+    op = sc.opacity.astype(np.float64)
+    worst = 0.0
+    for j in drop:
+        g = gg[j]
+        u = np.arange(16 * tx[j], 16 * tx[j] + 16)
+        v = np.arange(16 * ty[j], 16 * ty[j] + 16)
+        vv, uu = np.meshgrid(v, u, indexing="ij")
+        dx, dy = uu - m[g, 0], vv - m[g, 1]
+        q = con[g, 0] * dx * dx + 2 * con[g, 1] * dx * dy + con[g, 2] * dy * dy
+        worst = max(worst, float((op[g] * np.exp(-0.5 * q)).max() * 255.0))
+    assert worst < 1.0
 
 
 # -------------------------------------------------------- compositing
