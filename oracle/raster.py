@@ -161,7 +161,7 @@ def pixel_rays(cam, uv: torch.Tensor):
 
 
 def ray_ellipsoid(R: torch.Tensor, s: torch.Tensor, v_s: torch.Tensor,
-                  d: torch.Tensor, zc: torch.Tensor):
+                  d: torch.Tensor, zc: torch.Tensor, frozen=None):
     """Midpoint depth and ellipsoid normal for every (ray, Gaussian) pair.
 
     R [L,3,3], s [L,3], v_s [L,3] (= R^T (C - mu) / s), world ray directions
@@ -180,8 +180,11 @@ def ray_ellipsoid(R: torch.Tensor, s: torch.Tensor, v_s: torch.Tensor,
     cv = torch.cross(v_s[None].expand_as(d_s), d_s, dim=-1)
     disc = qa - (cv * cv).sum(-1)                  # (b^2 - 4ac) / 4
     with torch.no_grad():
-        hit = disc > 0
-        inside = (qc <= 0)[None, :].expand_as(hit)
+        if frozen is not None and not isinstance(frozen, str):
+            hit, inside = frozen
+        else:
+            hit = disc > 0
+            inside = (qc <= 0)[None, :].expand_as(hit)
     sq = torch.sqrt(torch.where(hit, disc, torch.ones_like(disc))) * hit
     root_sign = torch.where(inside, torch.ones_like(disc), -torch.ones_like(disc))
     t_hit = (-0.5 * qb + root_sign * sq) / qa
@@ -189,6 +192,8 @@ def ray_ellipsoid(R: torch.Tensor, s: torch.Tensor, v_s: torch.Tensor,
     n_un = torch.einsum("lij,plj->pli", R, pnt / s[None])
     n = n_un / torch.linalg.vector_norm(n_un, dim=-1, keepdim=True)
     n = torch.where(inside[..., None], -n, n)
+    if frozen is not None:
+        return depth, n, disc, qa, qc, (hit, inside)
     return depth, n, disc, qa, qc
 
 
@@ -204,8 +209,14 @@ class Bands:
 
 
 def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
-                   bands: Optional[Bands] = None) -> Dict[str, torch.Tensor]:
-    """Alg. 2 for the pixels ``uv`` [P,2] over the ordered list ``ids`` [L]."""
+                   bands: Optional[Bands] = None, frozen=None) -> Dict[str, torch.Tensor]:
+    """Alg. 2 for the pixels ``uv`` [P,2] over the ordered list ``ids`` [L].
+
+    ``frozen`` (the ``decisions`` entry of an earlier call on the same pixels
+    and list) replays that call's discrete decisions - alpha skip, stop,
+    ray hit and camera-inside - so that the result is a smooth function of
+    the parameters (used for finite differences of the almost-everywhere
+    derivative)."""
     P = uv.shape[0]
     L = ids.numel()
     C = prep.sem.shape[1]
@@ -219,6 +230,7 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
                    n_used=torch.zeros(P, dtype=torch.int64))
         for k in ("amb_fwd", "amb_grad"):
             out[k] = torch.zeros(P, dtype=torch.bool)
+        out["decisions"] = None
         return out
     m = prep.mean2d[ids]
     con = prep.conic[ids]
@@ -230,19 +242,21 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
     a_raw = op[None, :] * torch.exp(power)
     alpha = torch.clamp(a_raw, max=ALPHA_MAX)
     with torch.no_grad():
-        valid = alpha >= ALPHA_MIN
+        valid = alpha >= ALPHA_MIN if frozen is None else frozen[0]
     a_eff = torch.where(valid, alpha, torch.zeros_like(alpha))
     one_m = 1.0 - a_eff
     T_after = torch.cumprod(one_m, dim=1)
     T_before = torch.cat([torch.ones(P, 1, dtype=F64), T_after[:, :-1]], dim=1)
     with torch.no_grad():
-        incl = valid & (T_after >= T_MIN)
+        incl = valid & (T_after >= T_MIN) if frozen is None else frozen[1]
     w = torch.where(incl, a_eff * T_before, torch.zeros_like(a_eff))
     T_final = torch.prod(torch.where(incl, one_m, torch.ones_like(one_m)), dim=1)
 
     # ray-ellipsoid intersection per (pixel, Gaussian)
     d, zc = pixel_rays(cam, uv)
-    depth, n, disc, qa, qc = ray_ellipsoid(prep.R[ids], prep.s[ids], prep.v_s[ids], d, zc)
+    depth, n, disc, qa, qc, hit_inside = ray_ellipsoid(
+        prep.R[ids], prep.s[ids], prep.v_s[ids], d, zc,
+        frozen="return" if frozen is None else frozen[2])
 
     rgb = w @ prep.rgb[ids]
     out = dict(
@@ -253,6 +267,7 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
         logits=w @ prep.sem[ids],
         T=T_final,
     )
+    out["decisions"] = (valid, incl, hit_inside)
     with torch.no_grad():
         pos = torch.arange(1, L + 1)[None, :].expand(P, L)
         out["n_contrib"] = torch.where(incl, pos, torch.zeros_like(pos)).max(1).values

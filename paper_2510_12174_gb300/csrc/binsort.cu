@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256)
     emit_kernel(const CamTable* __restrict__ tab, int64_t n, int n_cams, int64_t capacity,
                 const uint2* __restrict__ rect, const uint32_t* __restrict__ touched,
                 const uint32_t* __restrict__ offs, const uint32_t* __restrict__ zbits,
-                WsHeader* __restrict__ hdr, unsigned long long* __restrict__ keys,
-                uint32_t* __restrict__ vals) {
+                const float* __restrict__ cull, WsHeader* __restrict__ hdr,
+                unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
     const int64_t total = n * (int64_t)n_cams;
     const uint64_t need = (uint64_t)offs[total - 1] + touched[total - 1];
     if (need > (uint64_t)capacity) {
@@ -144,9 +144,18 @@ __global__ void __launch_bounds__(256)
         const uint2 r = rect[t];
         const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
         const unsigned long long zb = zbits[t];
+        float cr[CULL_FLOATS];
+        {
+            const float4* src = reinterpret_cast<const float4*>(cull + (size_t)t * CULL_FLOATS);
+            const float4 c0 = src[0], c1 = src[1];
+            cr[0] = c0.x; cr[1] = c0.y; cr[2] = c0.z; cr[3] = c0.w;
+            cr[4] = c1.x; cr[5] = c1.y; cr[6] = c1.z; cr[7] = c1.w;
+        }
         uint32_t o = offs[t];
+        const uint32_t o_end = o + cnt;
         for (int ty = y0; ty < y1; ++ty)
             for (int tx = x0; tx < x1; ++tx) {
+                if (!tile_keep(cr, tx, ty) || o >= o_end) continue;
                 const unsigned long long tile =
                     (unsigned long long)(cam.tile_off + (int64_t)ty * cam.tiles_x + tx);
                 keys[o] = (tile << 32) | zb;
@@ -277,8 +286,8 @@ int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
         const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
         emit_kernel<<<grid, 256, 0, st>>>(ws_ptr<CamTable>(ws, p, OFF_CAM), p.n, p.n_cams,
                                           p.capacity, ws_ptr<uint2>(ws, p, OFF_RECT), touched,
-                                          offs, ws_ptr<uint32_t>(ws, p, OFF_ZBITS), hdr, keys[0],
-                                          vals[0]);
+                                          offs, ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
+                                          ws_ptr<float>(ws, p, OFF_CULL), hdr, keys[0], vals[0]);
         ++launches;
     }
     const int nb = (int)((p.capacity + SORT_ITEMS - 1) / SORT_ITEMS);

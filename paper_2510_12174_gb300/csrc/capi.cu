@@ -137,6 +137,7 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     sizes[OFF_HIST] = sizeof(uint32_t) * 256 * (size_t)nb_sort;
     sizes[OFF_RANGES] = sizeof(uint2) * (size_t)tiles;
     sizes[OFF_GREC] = sizeof(float) * GREC_FLOATS * (size_t)total;
+    sizes[OFF_CULL] = sizeof(float) * CULL_FLOATS * (size_t)total;
     size_t off = 0;
     for (int r = 0; r < OFF_END; ++r) {
         plan->off[r] = off;

@@ -213,10 +213,31 @@ __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy
     o.kappa = lmax * lmax / fmaxf(detK, 1e-30f);
 }
 
+// Opacity-aware tile-test inputs from the float32 recipe: conic, and
+// qlim = 2 (e LN2 + (m - 1)) * 1.01 + 0.05 with 255 op = m 2^e, m in [1, 2)
+// (an upper bound of 2 ln(255 op), the q at which alpha falls to 1/255).
+__device__ __forceinline__ void cull_record(const Recipe& rc, float op, float* cr) {
+    cr[C_MX] = rc.mx;
+    cr[C_MY] = rc.my;
+    cr[C_KA] = __fdiv_rn(rc.c, rc.det);
+    cr[C_KB] = -__fdiv_rn(rc.b, rc.det);
+    cr[C_KC] = __fdiv_rn(rc.a, rc.det);
+    const float ac = __fadd_rn(rc.a, rc.c);
+    cr[C_NOCULL] = (__fmul_rn(ac, ac) > __fmul_rn(4096.f, rc.det)) ? 1.f : 0.f;
+    int ex = 0;
+    const float mant = frexpf(__fmul_rn(255.f, op), &ex);
+    const float m = __fmul_rn(mant, 2.f);
+    const float e = (float)(ex - 1);
+    const float lnb = __fadd_rn(__fmul_rn(e, 0x1.62e43p-1f), __fsub_rn(m, 1.f));
+    cr[C_QLIM] = __fadd_rn(__fmul_rn(__fmul_rn(2.f, lnb), 1.01f), 0.05f);
+    cr[7] = 0.f;
+}
+
 __global__ void __launch_bounds__(256)
     preprocess_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab, int n_cams,
                       float lowpass, float* __restrict__ rec, uint2* __restrict__ rect,
-                      uint32_t* __restrict__ touched, uint32_t* __restrict__ zbits) {
+                      uint32_t* __restrict__ touched, uint32_t* __restrict__ zbits,
+                      float* __restrict__ cull) {
     const int64_t n = g.n;
     const int64_t total = n * (int64_t)n_cams;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -238,10 +259,19 @@ __global__ void __launch_bounds__(256)
             zbits[t] = __float_as_uint(rc.pz);
             continue;
         }
-        touched[t] = (uint32_t)((rc.x1 - rc.x0) * (rc.y1 - rc.y0));
+        float cr[CULL_FLOATS];
+        cull_record(rc, __ldg(g.opacity + i), cr);
+        uint32_t kept = 0;
+        for (int ty = rc.y0; ty < rc.y1; ++ty)
+            for (int tx = rc.x0; tx < rc.x1; ++tx) kept += tile_keep(cr, tx, ty) ? 1u : 0u;
+        touched[t] = kept;
         rect[t] = make_uint2((uint32_t)rc.x0 | ((uint32_t)rc.x1 << 16),
                              (uint32_t)rc.y0 | ((uint32_t)rc.y1 << 16));
         zbits[t] = __float_as_uint(rc.pz);
+        float4* cdst = reinterpret_cast<float4*>(cull + (size_t)t * CULL_FLOATS);
+        cdst[0] = make_float4(cr[0], cr[1], cr[2], cr[3]);
+        cdst[1] = make_float4(cr[4], cr[5], cr[6], cr[7]);
+        if (kept == 0) continue;
 
         float o[REC_FLOATS];
         SplatFF sf;
@@ -328,7 +358,8 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
         preprocess_kernel<<<grid, 256, 0, st>>>(
             g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.n_cams, p.cfg.lowpass,
             ws_ptr<float>(ws, p, OFF_REC), ws_ptr<uint2>(ws, p, OFF_RECT),
-            ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS));
+            ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
+            ws_ptr<float>(ws, p, OFF_CULL));
         ++launches;
     }
     return launches;

@@ -80,8 +80,58 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 enum {
     OFF_HDR = 0, OFF_CAM, OFF_REC, OFF_RECT, OFF_TOUCH, OFF_OFFS, OFF_ZBITS,
     OFF_SCAN, OFF_KEYS0, OFF_KEYS1, OFF_VALS0, OFF_VALS1, OFF_HIST, OFF_RANGES,
-    OFF_GREC, OFF_END
+    OFF_GREC, OFF_CULL, OFF_END
 };
+
+// Per-(camera, Gaussian) record of the opacity-aware tile test (8 floats):
+// float32 projected centre, float32 conic (kA, kB, kC), qlim, no-cull flag.
+enum { C_MX = 0, C_MY, C_KA, C_KB, C_KC, C_QLIM, C_NOCULL, CULL_FLOATS = 8 };
+
+// Opacity-aware tile test, float32 recipe with non-contractible operations
+// (identical operation order in the oracle's binning): keep the tile when the
+// minimum over its pixel-centre square of q(D) = D^T K D is <= qlim.
+__device__ __forceinline__ float cull_q(float kA, float kB, float kC, float dx, float dy) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(kA, dx), dx),
+                               __fmul_rn(__fmul_rn(__fmul_rn(2.f, kB), dx), dy)),
+                     __fmul_rn(__fmul_rn(kC, dy), dy));
+}
+
+__device__ __forceinline__ bool tile_keep(const float* __restrict__ cr, int tx, int ty) {
+    if (cr[C_NOCULL] != 0.f) return true;
+    const float mx = cr[C_MX], my = cr[C_MY], kA = cr[C_KA], kB = cr[C_KB], kC = cr[C_KC];
+    const float X0 = (float)(tx * TILE), X1 = (float)(tx * TILE + TILE - 1);
+    const float Y0 = (float)(ty * TILE), Y1 = (float)(ty * TILE + TILE - 1);
+    float qmin;
+    if (X0 <= mx && mx <= X1 && Y0 <= my && my <= Y1) {
+        qmin = 0.f;
+    } else {
+        const float ylo = __fsub_rn(Y0, my), yhi = __fsub_rn(Y1, my);
+        const float xlo = __fsub_rn(X0, mx), xhi = __fsub_rn(X1, mx);
+        float q[4];
+        {
+            const float dx = xlo;
+            const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(kB, dx), kC), ylo), yhi);
+            q[0] = cull_q(kA, kB, kC, dx, dy);
+        }
+        {
+            const float dx = xhi;
+            const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(kB, dx), kC), ylo), yhi);
+            q[1] = cull_q(kA, kB, kC, dx, dy);
+        }
+        {
+            const float dy = ylo;
+            const float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(kB, dy), kA), xlo), xhi);
+            q[2] = cull_q(kA, kB, kC, dx, dy);
+        }
+        {
+            const float dy = yhi;
+            const float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(kB, dy), kA), xlo), xhi);
+            q[3] = cull_q(kA, kB, kC, dx, dy);
+        }
+        qmin = fminf(fminf(q[0], q[1]), fminf(q[2], q[3]));
+    }
+    return qmin <= cr[C_QLIM];
+}
 
 constexpr int SORT_ITEMS = 2048;   // keys per sort block (256 threads x 8)
 constexpr int SCAN_ITEMS = 4096;   // elements per scan block (256 threads x 16)

@@ -167,7 +167,7 @@ def test_backward_parity_two_cameras_with_depth_normal():
 
 def test_backward_parity_bf16_features():
     sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=16, seed=17, feat_bf16=True)
-    check_grad_errors(_grad_case(sc, cams))
+    check_grad_errors(_grad_case(sc, cams), norm=3e-4)
 
 
 def test_capacity_overflow_reports_and_recovers():
@@ -264,76 +264,113 @@ def test_full_size_sampled_pixels(n):
 
 
 def test_full_size_finite_differences_64_params():
-    """1M Gaussians at 1280x720, 64 logits: the analytic gradient against GPU
-    central differences of L = sum_c <output_c, upstream_c> on 64 parameters
-    drawn from Gaussians that contribute, stratified over mu, q, s, opacity,
-    SH, logits and k.  The forward is deterministic, so pixels the
-    perturbation does not reach cancel exactly in L(+h) - L(-h) (summed in
-    float64); a pair of steps h and h/2 that disagree marks a discrete change
-    (a tile rectangle, the alpha threshold) and the sample is redrawn."""
+    """1M Gaussians at 1280x720, 64 logits (the benchmark scene): the GPU
+    gradient against central finite differences on 64 parameters, stratified
+    over mu, q, s, opacity, SH, logits and k of Gaussians drawn from a band of
+    tiles.  The differences are taken on the float64 oracle over the tiles
+    whose lists hold the Gaussian, with the discrete decisions (alpha skip,
+    stop, ray hit) frozen at the unperturbed state: the forward is
+    discontinuous where a pixel crosses alpha = 1/255, and the analytic
+    gradient is the derivative almost everywhere.  Upstream gradients are
+    zeroed on ambiguous pixels for both sides."""
     sc, cams = scenes.config3()
+    cam = cams[0]
+    b = oracle.bin_cameras_fast(sc, cams)
+    vals, ranges = b["vals"], b["ranges"]
+    up = scenes.upstream_grads(cams, sc.n_sem, seed=31)
+    TX = (cam.width + 15) // 16
+    rng = np.random.default_rng(3)
+    band = [t for t in range(20 * TX + 30, 20 * TX + 50)]
+    cand = np.unique(np.concatenate([vals[ranges[t][0]:ranges[t][1]] for t in band]))
+    picks = rng.choice(cand, 64, replace=False)
+
+    def tiles_of(g):
+        pos = np.nonzero(vals == g)[0]
+        return np.unique(np.searchsorted(ranges[:, 1], pos, side="right"))
+
+    tiles = {int(g): tiles_of(g) for g in picks}
+    all_tiles = np.unique(np.concatenate(list(tiles.values())))
+    params = orr.Params.from_scene(sc)
+    with torch.no_grad():
+        prep = orr.preprocess(params, cam)
+    # ambiguous pixels of the involved tiles -> zero upstream there
+    base = {}
+    for t in all_tiles:
+        s0, s1 = ranges[t]
+        ids = torch.as_tensor(vals[s0:s1].astype(np.int64))
+        uu, vv = orr.tile_pixels(cam, int(t))
+        uv = torch.as_tensor(np.stack([uu, vv], 1), dtype=torch.float64)
+        with torch.no_grad():
+            r = orr.composite_tile(prep, ids, uv, cam)
+        amb = r["amb_grad"].numpy()
+        for key in ("rgb", "depth", "normal_g", "kmap", "logits"):
+            a = up[key][0]
+            if a.ndim == 3:
+                a[:, vv[amb], uu[amb]] = 0
+            else:
+                a[vv[amb], uu[amb]] = 0
+        base[int(t)] = (uu, vv, uv, r["decisions"])
+    up["normal_d"][0][:] = 0
+    # GPU gradient with the masked upstream
     ds = rz.DeviceScene.from_scene(sc)
     r = rz.Renderer(ds, cams)
-    up = flat_upstream(scenes.upstream_grads(cams, sc.n_sem, seed=31),
-                       keys=("rgb", "depth", "normal_g", "kmap", "logits"))
-    out = r.forward(normal_d=False)
-    grads = r.backward(out, up)
+    out = r.forward()
+    grads = r.backward(out, flat_upstream(up))
     torch.cuda.synchronize()
-    keys, vals, _ = r.sorted_instances()
-    nc = out["n_contrib"]
-    del out
+    g_gpu = {k: v.cpu().numpy() for k, v in grads.items()}
+    rms = {k: float(np.sqrt(np.mean(v.astype(np.float64) ** 2))) for k, v in g_gpu.items()}
 
-    def loss():
-        o = r.forward(normal_d=False)
-        return sum(float((o[k].double() * up[k].double()).sum()) for k in up)
+    def local_loss(g, name, idx, value):
+        """Oracle loss over Gaussian g's tiles with parameter (name, idx) set."""
+        ts = tiles[g]
+        ids_all = np.unique(np.concatenate([vals[ranges[t][0]:ranges[t][1]] for t in ts]))
+        sub = sc.subset(ids_all)
+        sub = scenes.Scene(**{k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v)
+                              for k, v in sub.__dict__.items()})
+        j = int(np.searchsorted(ids_all, g))
+        arr = getattr(sub, name)
+        if name in ("mean", "quat", "scale"):
+            arr[idx[0], j] = value
+        elif arr.ndim == 1:
+            arr[j] = value
+        else:
+            arr[(j,) + tuple(idx[1:])] = value
+        with torch.no_grad():
+            pl = orr.preprocess(orr.Params.from_scene(sub), cam)
+        tot = 0.0
+        for t in ts:
+            s0, s1 = ranges[t]
+            ids = torch.as_tensor(np.searchsorted(ids_all, vals[s0:s1]).astype(np.int64))
+            uu, vv, uv, dec = base[int(t)]
+            with torch.no_grad():
+                o = orr.composite_tile(pl, ids, uv, cam, frozen=dec)
+            for key, okey in (("rgb", "rgb"), ("depth", "depth"), ("normal_g", "normal"),
+                              ("kmap", "kmap"), ("logits", "logits")):
+                a = up[key][0]
+                gg = a[:, vv, uu].T if a.ndim == 3 else a[vv, uu]
+                val = o[okey].numpy()
+                tot += float((val * gg).sum())
+        return tot
 
-    rng = np.random.default_rng(3)
-    cand = np.unique(vals)
     names = ["mean", "quat", "scale", "opacity", "sh", "sem", "kfac"]
-    checked = {n: 0 for n in names}
     worst = 0.0
-    tries = 0
-    while min(checked.values()) < 9 and tries < 400:
-        tries += 1
-        name = names[tries % len(names)]
-        if checked[name] >= 10:
-            continue
-        g = int(rng.choice(cand))
-        t = getattr(ds, name)
-        if t.dim() == 1:
+    for n_done, g in enumerate(picks):
+        g = int(g)
+        name = names[n_done % len(names)]
+        t = getattr(sc, name)
+        if name in ("mean", "quat", "scale"):
+            idx = (int(rng.integers(0, 3 if name != "quat" else 4)), g)
+        elif t.ndim == 1:
             idx = (g,)
-        elif name in ("mean", "quat", "scale"):
-            idx = (int(rng.integers(0, t.shape[0])), g)
         elif name == "sh":
             idx = (g, int(rng.integers(0, t.shape[1])), int(rng.integers(0, 3)))
         else:
             idx = (g, int(rng.integers(0, t.shape[1])))
-        an = float(grads[name][idx])
         x0 = float(t[idx])
-        def fd(h):
-            t[idx] = x0 + h
-            lp = loss()
-            t[idx] = x0 - h
-            lm = loss()
-            t[idx] = x0
-            return (lp - lm) / (2 * h)
-        if name == "mean":
-            h = 2e-4
-        elif name in ("sem", "kfac", "sh"):
-            h = 5e-2  # the outputs are (piecewise) linear in these: a large step
-        else:
-            h = 2e-3 * max(abs(x0), 1e-2)
-        f1, f2 = fd(h), fd(h / 2)
-        # an alpha-threshold, termination or tile-rectangle crossing inside the
-        # stencil adds jump / 2h to the difference quotient; such samples show
-        # as disagreement between the two steps (float32 noise here is ~2e-4)
-        if abs(f1 - f2) > 3e-3 * max(abs(f1), abs(f2), 1e-3):
-            continue
-        if abs(f2) < 1e-3 and abs(an) < 1e-3:
-            continue  # no signal to compare
-        rel = abs(an - f2) / max(abs(f2), 1e-2)
+        h = 1e-6 * max(abs(x0), 1.0) if name != "mean" else 1e-7
+        fd = (local_loss(g, name, idx, x0 + h) - local_loss(g, name, idx, x0 - h)) / (2 * h)
+        an = float(g_gpu[name][idx])
+        rel = abs(an - fd) / max(abs(fd), 1e-2 * rms[name])
         worst = max(worst, rel)
-        checked[name] += 1
-        assert rel < 2e-2, (name, idx, an, f1, f2)
-    print("FD checked", checked, "worst rel", worst)
-    assert sum(checked.values()) >= 64
+        assert rel < 1e-2, (name, idx, an, fd, rms[name])
+    print("FD 64 params: worst rel", worst)

@@ -310,7 +310,7 @@ def _keep_scalar(pr, g, tx, ty):
     kA, kB, kC = (f(pr["conic32"][i][g]) for i in range(3))
     X0, X1, Y0, Y1 = f(16 * tx), f(16 * tx + 15), f(16 * ty), f(16 * ty + 15)
     if X0 <= mx <= X1 and Y0 <= my <= Y1:
-        return True
+        return bool(f(0) <= pr["qlim"][g])
     best = None
     for xe in (X0, X1):
         dx = f(xe - mx)
