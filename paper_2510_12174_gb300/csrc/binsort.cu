@@ -134,34 +134,78 @@ __global__ void __launch_bounds__(256)
         hdr->n_instances = (uint32_t)need;
         hdr->need = need;
     }
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t cnt = touched[t];
-        if (cnt == 0) continue;
-        const int k = (int)(t / n);
-        const uint32_t g = (uint32_t)(t - (int64_t)k * n);
-        const DevCam& cam = tab->cam[k];
-        const uint2 r = rect[t];
-        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-        const unsigned long long zb = zbits[t];
-        float cr[CULL_FLOATS];
-        {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    // uniform loop bound: whole warps iterate together, so rectangles larger
+    // than 32 tiles are emitted cooperatively (ballot compaction keeps the
+    // row-major order)
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        const uint32_t cnt = t < total ? touched[t] : 0u;
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0, k = 0;
+        uint32_t g = 0, o = 0;
+        unsigned long long zb = 0, toff = 0;
+        int tiles_x = 0;
+        float cr[CULL_FLOATS] = {};
+        if (cnt) {
+            k = (int)(t / n);
+            g = (uint32_t)(t - (int64_t)k * n);
+            const DevCam& cam = tab->cam[k];
+            const uint2 r = rect[t];
+            x0 = r.x & 0xffff; x1 = r.x >> 16; y0 = r.y & 0xffff; y1 = r.y >> 16;
+            zb = zbits[t];
+            toff = (unsigned long long)cam.tile_off;
+            tiles_x = cam.tiles_x;
+            o = offs[t];
             const float4* src = reinterpret_cast<const float4*>(cull + (size_t)t * CULL_FLOATS);
             const float4 c0 = src[0], c1 = src[1];
             cr[0] = c0.x; cr[1] = c0.y; cr[2] = c0.z; cr[3] = c0.w;
             cr[4] = c1.x; cr[5] = c1.y; cr[6] = c1.z; cr[7] = c1.w;
         }
-        uint32_t o = offs[t];
-        const uint32_t o_end = o + cnt;
-        for (int ty = y0; ty < y1; ++ty)
-            for (int tx = x0; tx < x1; ++tx) {
-                if (!tile_keep(cr, tx, ty) || o >= o_end) continue;
-                const unsigned long long tile =
-                    (unsigned long long)(cam.tile_off + (int64_t)ty * cam.tiles_x + tx);
-                keys[o] = (tile << 32) | zb;
-                vals[o] = g;
-                ++o;
+        const int nt = (x1 - x0) * (y1 - y0);
+        if (cnt && nt <= 32) {
+            const uint32_t o_end = o + cnt;
+            for (int ty = y0; ty < y1; ++ty)
+                for (int tx = x0; tx < x1; ++tx) {
+                    if (!tile_keep(cr, tx, ty) || o >= o_end) continue;
+                    const unsigned long long tile = toff + (unsigned long long)(ty * tiles_x + tx);
+                    keys[o] = (tile << 32) | zb;
+                    vals[o] = g;
+                    ++o;
+                }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, cnt && nt > 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            float cb[CULL_FLOATS];
+#pragma unroll
+            for (int q = 0; q < CULL_FLOATS; ++q) cb[q] = __shfl_sync(0xffffffffu, cr[q], src);
+            const int bx0 = __shfl_sync(0xffffffffu, x0, src);
+            const int by0 = __shfl_sync(0xffffffffu, y0, src);
+            const int bw = __shfl_sync(0xffffffffu, x1 - x0, src);
+            const int bn = __shfl_sync(0xffffffffu, nt, src);
+            const int btx = __shfl_sync(0xffffffffu, tiles_x, src);
+            const unsigned long long btoff = __shfl_sync(0xffffffffu, toff, src);
+            const unsigned long long bzb = __shfl_sync(0xffffffffu, zb, src);
+            const uint32_t bg = __shfl_sync(0xffffffffu, g, src);
+            uint32_t bo = __shfl_sync(0xffffffffu, o, src);
+            const uint32_t bend = bo + __shfl_sync(0xffffffffu, cnt, src);
+            for (int j0 = 0; j0 < bn; j0 += 32) {
+                const int j = j0 + lane;
+                const int tx = bx0 + j % bw, ty = by0 + j / bw;
+                const bool keep = j < bn && tile_keep(cb, tx, ty);
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                const uint32_t dst = bo + __popc(m & lt_mask);
+                if (keep && dst < bend) {
+                    const unsigned long long tile = btoff + (unsigned long long)(ty * btx + tx);
+                    keys[dst] = (tile << 32) | bzb;
+                    vals[dst] = bg;
+                }
+                bo += __popc(m);
             }
+        }
     }
 }
 

@@ -135,6 +135,7 @@ struct SplatFF {
     float mxh, myh, mxl, myl;
     ff A, B, C;
     float kappa;
+    float cxx, cyy;  // diagonal of the 2D covariance
 };
 
 __device__ __forceinline__ void split_center(ff m, float* hi, float* lo) {
@@ -201,6 +202,8 @@ __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy
     const ff c01 = ff_add(ff_add(ff_mul(V[0][0], V[1][0]), ff_mul(V[0][1], V[1][1])),
                           ff_mul(V[0][2], V[1][2]));
     const ff det = ff_sub(ff_mul(c00, c11), ff_mul(c01, c01));
+    o.cxx = ff_val(c00);
+    o.cyy = ff_val(c11);
     o.A = ff_div(c11, det);
     o.B = ff_neg(ff_div(c01, det));
     o.C = ff_div(c00, det);
@@ -233,6 +236,17 @@ __device__ __forceinline__ void cull_record(const Recipe& rc, float op, float* c
     cr[7] = 0.f;
 }
 
+// Number of kept tiles of the rectangle [x0,x1) x [y0,y1) (opacity-aware test).
+__device__ __forceinline__ uint32_t count_kept_serial(const float* cr, int x0, int x1, int y0,
+                                                      int y1) {
+    uint32_t kept = 0;
+    for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx) kept += tile_keep(cr, tx, ty) ? 1u : 0u;
+    return kept;
+}
+
+constexpr int COOP_TILES = 32;  // rectangles above this are tested by the whole warp
+
 __global__ void __launch_bounds__(256)
     preprocess_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab, int n_cams,
                       float lowpass, float* __restrict__ rec, uint2* __restrict__ rect,
@@ -240,30 +254,60 @@ __global__ void __launch_bounds__(256)
                       float* __restrict__ cull) {
     const int64_t n = g.n;
     const int64_t total = n * (int64_t)n_cams;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t / n);
-        const int64_t i = t - (int64_t)k * n;
+    const int lane = threadIdx.x & 31;
+    // the loop bound is uniform across the block, so whole warps iterate
+    // together and can test large rectangles cooperatively
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        const bool act = t < total;
+        const int k = act ? (int)(t / n) : 0;
+        const int64_t i = act ? t - (int64_t)k * n : 0;
         const DevCam& cam = tab->cam[k];
-        const float mux = __ldg(g.mean + i), muy = __ldg(g.mean + n + i),
-                    muz = __ldg(g.mean + 2 * n + i);
-        const float qw = __ldg(g.quat + i), qx = __ldg(g.quat + n + i),
-                    qy = __ldg(g.quat + 2 * n + i), qz = __ldg(g.quat + 3 * n + i);
-        const float sx = __ldg(g.scale + i), sy = __ldg(g.scale + n + i),
-                    sz = __ldg(g.scale + 2 * n + i);
-        Recipe rc;
-        binning_recipe(cam, mux, muy, muz, qw, qx, qy, qz, sx, sy, sz, lowpass, rc);
+        Recipe rc = {};
+        float cr[CULL_FLOATS] = {};
+        float mux = 0.f, muy = 0.f, muz = 0.f, qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f;
+        float sx = 1.f, sy = 1.f, sz = 1.f;
+        int nt = 0;
+        if (act) {
+            mux = __ldg(g.mean + i); muy = __ldg(g.mean + n + i); muz = __ldg(g.mean + 2 * n + i);
+            qw = __ldg(g.quat + i); qx = __ldg(g.quat + n + i);
+            qy = __ldg(g.quat + 2 * n + i); qz = __ldg(g.quat + 3 * n + i);
+            sx = __ldg(g.scale + i); sy = __ldg(g.scale + n + i); sz = __ldg(g.scale + 2 * n + i);
+            binning_recipe(cam, mux, muy, muz, qw, qx, qy, qz, sx, sy, sz, lowpass, rc);
+            if (rc.valid) {
+                cull_record(rc, __ldg(g.opacity + i), cr);
+                nt = (rc.x1 - rc.x0) * (rc.y1 - rc.y0);
+            }
+        }
+        uint32_t kept = (nt > 0 && nt <= COOP_TILES)
+                            ? count_kept_serial(cr, rc.x0, rc.x1, rc.y0, rc.y1) : 0u;
+        unsigned big = __ballot_sync(0xffffffffu, nt > COOP_TILES);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            float cb[CULL_FLOATS];
+#pragma unroll
+            for (int q = 0; q < CULL_FLOATS; ++q) cb[q] = __shfl_sync(0xffffffffu, cr[q], src);
+            const int bx0 = __shfl_sync(0xffffffffu, rc.x0, src);
+            const int by0 = __shfl_sync(0xffffffffu, rc.y0, src);
+            const int bw = __shfl_sync(0xffffffffu, rc.x1 - rc.x0, src);
+            const int bn = __shfl_sync(0xffffffffu, nt, src);
+            uint32_t cnt = 0;
+            for (int j0 = 0; j0 < bn; j0 += 32) {
+                const int j = j0 + lane;
+                const bool keep = j < bn && tile_keep(cb, bx0 + j % bw, by0 + j / bw);
+                cnt += __popc(__ballot_sync(0xffffffffu, keep));
+            }
+            if (lane == src) kept = cnt;
+        }
+        if (!act) continue;
         if (!rc.valid) {
             touched[t] = 0;
             rect[t] = make_uint2(0, 0);
             zbits[t] = __float_as_uint(rc.pz);
             continue;
         }
-        float cr[CULL_FLOATS];
-        cull_record(rc, __ldg(g.opacity + i), cr);
-        uint32_t kept = 0;
-        for (int ty = rc.y0; ty < rc.y1; ++ty)
-            for (int tx = rc.x0; tx < rc.x1; ++tx) kept += tile_keep(cr, tx, ty) ? 1u : 0u;
         touched[t] = kept;
         rect[t] = make_uint2((uint32_t)rc.x0 | ((uint32_t)rc.x1 << 16),
                              (uint32_t)rc.y0 | ((uint32_t)rc.y1 << 16));
@@ -324,8 +368,13 @@ __global__ void __launch_bounds__(256)
             for (int b = 0; b < 3; ++b) o[R_NW + a * 3 + b] = rc.R[a][b] * is[b];
         }
         o[R_Z] = rc.pz;
-        o[38] = 0.f;
-        o[39] = 0.f;
+        {
+            // box of the q <= qlim ellipse (x half-extent sqrt(qlim * Sigma_xx)),
+            // with a relative and a one-pixel margin
+            const float ql = fmaxf(cr[C_QLIM], 0.f);
+            o[R_EXTX] = sqrtf(ql * sf.cxx) * 1.01f + 1.f;
+            o[R_EXTY] = sqrtf(ql * sf.cyy) * 1.01f + 1.f;
+        }
         float4* dst = reinterpret_cast<float4*>(rec + (size_t)t * REC_FLOATS);
 #pragma unroll
         for (int q = 0; q < REC_FLOATS / 4; ++q)

@@ -99,7 +99,12 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
     const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
     const int64_t ltile = gtile - cam.tile_off;
     const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
-    const int u = tx * TILE + (tid & 15), v = ty * TILE + (tid >> 4);
+    int lx, ly;
+    tile_pixel(tid, &lx, &ly);
+    const int u = tx * TILE + lx, v = ty * TILE + ly;
+    // the warp's 8x4 pixel block, for the per-warp bounding-box skip
+    const float bx0 = (float)(tx * TILE + ((tid >> 5) & 1) * 8);
+    const float by0 = (float)(ty * TILE + (tid >> 6) * 4);
     const bool inside = u < cam.width && v < cam.height;
     const float uf = (float)u, vf = (float)v;
     const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
@@ -166,6 +171,7 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
             for (int j = count - 1; j >= 0; --j) {
                 const uint32_t pos = (uint32_t)(b * BBATCH + j);
                 const float* rc = &S.rec[buf][j][0];
+                if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
                 float gv[32];
 #pragma unroll
                 for (int k = 0; k < 32; ++k) gv[k] = 0.f;

@@ -26,12 +26,33 @@ constexpr int TILE_PIX = TILE * TILE;
 //   [33]    camera-frame z of the centre
 //   [34..36] low words of the conic (double-float A, B, C)
 //   [37]    1 when the splat is ill-conditioned (alpha evaluated in
-//           double-float), else 0      [38..39] unused
+//           double-float), else 0
+//   [38..39] half-extents (x, y) of the box holding every pixel where alpha
+//           can reach alpha_min (with margin): a warp whose 8x4 pixel block
+//           lies outside skips the Gaussian
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_OP, R_K, R_RGB, R_CON = 9, R_MC = 12,
-    R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34, R_FLAG = 37, REC_FLOATS = 40
+    R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34, R_FLAG = 37, R_EXTX = 38, R_EXTY = 39,
+    REC_FLOATS = 40
 };
+
+// Pixel of thread tid inside its 16x16 tile: warp w covers the 8x4 block at
+// ((w & 1) * 8, (w >> 1) * 4), lanes row-major within the block.
+__device__ __forceinline__ void tile_pixel(int tid, int* lx, int* ly) {
+    const int w = tid >> 5, lane = tid & 31;
+    *lx = (w & 1) * 8 + (lane & 7);
+    *ly = (w >> 1) * 4 + (lane >> 3);
+}
+
+// True when the Gaussian cannot reach alpha_min anywhere in the warp's block
+// [bx0, bx0+7] x [by0, by0+3] (uniform across the warp).
+__device__ __forceinline__ bool warp_block_misses(const float* __restrict__ rc, float bx0,
+                                                  float by0) {
+    const float mx = rc[R_MXH] + rc[R_MXL], my = rc[R_MYH] + rc[R_MYL];
+    const float ex = rc[R_EXTX], ey = rc[R_EXTY];
+    return (bx0 + 7.f < mx - ex) || (bx0 > mx + ex) || (by0 + 3.f < my - ey) || (by0 > my + ey);
+}
 
 // Conic eigenvalue ratio above which alpha is evaluated in double-float: the
 // float32 quadratic form loses about log2(ratio) bits along the long axis.
