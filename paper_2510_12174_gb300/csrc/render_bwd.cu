@@ -50,12 +50,45 @@ struct BwdParams {
 
 template <int NS, typename FT>
 struct BwdSmem {
+    static constexpr int GOP = NS + 4;  // padded pitch: row reads and column gathers
+                                        // both avoid bank conflicts
     float rec[2][BBATCH][REC_FLOATS];
     FT sem[2][BBATCH][NS];
+    float gO[TILE_PIX][GOP];            // dL/dlogits of the tile's pixels, by thread
     uint32_t ids[2][BBATCH];
     uint64_t bar[2];
     uint32_t max_last;
 };
+
+// dot(gO row, semantic row) with 16-byte shared-memory loads.
+template <int NS>
+__device__ __forceinline__ float sem_dot(const float* go, const float* row) {
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < NS / 4; ++c) {
+        const float4 a = reinterpret_cast<const float4*>(go)[c];
+        const float4 b = reinterpret_cast<const float4*>(row)[c];
+        acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+    }
+    return acc;
+}
+template <int NS>
+__device__ __forceinline__ float sem_dot(const float* go, const __nv_bfloat16* row) {
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < NS / 8; ++c) {
+        const float4 a0 = reinterpret_cast<const float4*>(go)[2 * c];
+        const float4 a1 = reinterpret_cast<const float4*>(go)[2 * c + 1];
+        const uint4 bb = reinterpret_cast<const uint4*>(row)[c];
+        const float2 b0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.x));
+        const float2 b1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.y));
+        const float2 b2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.z));
+        const float2 b3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.w));
+        acc = fmaf(a0.x, b0.x, fmaf(a0.y, b0.y, fmaf(a0.z, b1.x, fmaf(a0.w, b1.y, acc))));
+        acc = fmaf(a1.x, b2.x, fmaf(a1.y, b2.y, fmaf(a1.z, b3.x, fmaf(a1.w, b3.y, acc))));
+    }
+    return acc;
+}
 
 template <int NS, typename FT>
 __device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, FT>& S, int buf,
@@ -90,7 +123,7 @@ __device__ __forceinline__ void cross_acc(const float* a, const float* b, float*
 }
 
 template <int NS, typename FT>
-__global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
+__global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BwdSmem<NS, FT>& S = *reinterpret_cast<BwdSmem<NS, FT>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -116,9 +149,12 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
     float T = 1.f;
     uint32_t last = 0;
     float g_rgb[3] = {0.f, 0.f, 0.f}, g_D = 0.f, g_N[3] = {0.f, 0.f, 0.f}, g_K = 0.f;
-    float g_O[NS];
-#pragma unroll
-    for (int c = 0; c < NS; ++c) g_O[c] = 0.f;
+    // upstream logit gradients of this pixel -> shared memory row tid (zero
+    // padded), read by this thread for G_i and by the warp's channel gather
+#pragma unroll 8
+    for (int c = 0; c < BwdSmem<NS, FT>::GOP; ++c)
+        S.gO[tid][c] = (inside && P.go.logits && c < P.n_sem)
+                           ? P.go.logits[pix * (int64_t)P.n_sem + c * HW + idx] : 0.f;
     if (inside) {
         T = P.T_final[pix + idx];
         last = P.n_contrib[pix + idx];
@@ -130,10 +166,6 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) g_N[c] = P.go.normal_g[pix * 3 + c * HW + idx];
         if (P.go.kmap) g_K = P.go.kmap[pix + idx];
-        if (P.go.logits)
-#pragma unroll
-            for (int c = 0; c < NS; ++c)
-                if (c < P.n_sem) g_O[c] = P.go.logits[pix * (int64_t)P.n_sem + c * HW + idx];
     }
 
     if (tid == 0) {
@@ -193,12 +225,10 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
 #pragma unroll
                         for (int i = 0; i < 3; ++i) nh[i] = G.m[i] * G.inv_m;
                         // G_i: upstream gradient . features of Gaussian i
-                        const FT* srow = &S.sem[buf][j][0];
-                        float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
-                                   g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
-                                   sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]);
-#pragma unroll
-                        for (int c = 0; c < NS; ++c) Gi = fmaf(g_O[c], to_f(srow[c]), Gi);
+                        const float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
+                                         g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
+                                         sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
+                                         sem_dot<NS>(&S.gO[tid][0], &S.sem[buf][j][0]);
                         const float dL_da = T * Gi - Sacc / om;
                         Sacc = fmaf(w, Gi, Sacc);
                         // alpha = min(alpha_max, op * Gs)
@@ -284,24 +314,34 @@ __global__ void __launch_bounds__(256, 1) render_bwd_kernel(const BwdParams P) {
                         }
                     }
                 }
-                if (__any_sync(0xffffffffu, contrib)) {
+                const unsigned cmask = __ballot_sync(0xffffffffu, contrib);
+                if (cmask) {
                     const uint32_t g = S.ids[buf][j];
                     const size_t rix = (size_t)cam_idx * (size_t)P.n + g;
                     const float tot = warp_reduce_transpose32(gv, lane);
                     if (tot != 0.f) atomicAdd(P.grec + rix * GREC_FLOATS + lane, tot);
                     if (P.n_sem > 0) {
-                        const FT* srow = &S.sem[buf][j][0];
-                        (void)srow;
-#pragma unroll
-                        for (int h = 0; h < (NS + 31) / 32; ++h) {
-                            float sv[32];
-#pragma unroll
-                            for (int k = 0; k < 32; ++k)
-                                sv[k] = (h * 32 + k < NS) ? w * g_O[(h * 32 + k) % NS] : 0.f;
-                            const float st = warp_reduce_transpose32(sv, lane);
-                            const int c = h * 32 + lane;
-                            if (c < P.n_sem && st != 0.f)
-                                atomicAdd(P.gsem + (size_t)g * P.n_sem + c, st);
+                        // dL/do_j[c] = sum over the contributing pixels l of w_l gO_l[c]:
+                        // lane L gathers channels 2L, 2L+1 (w_l by shuffle)
+                        float a0 = 0.f, a1 = 0.f;
+                        unsigned m = cmask;
+                        while (m) {
+                            const int l = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float wl = __shfl_sync(0xffffffffu, w, l);
+                            const float2 go =
+                                *reinterpret_cast<const float2*>(&S.gO[warp * 32 + l][2 * lane]);
+                            a0 = fmaf(wl, go.x, a0);
+                            a1 = fmaf(wl, go.y, a1);
+                        }
+                        const int c = 2 * lane;
+                        float* dst = P.gsem + (size_t)g * P.n_sem + c;
+                        if (c + 1 < P.n_sem && (P.n_sem & 1) == 0) {
+                            if (a0 != 0.f || a1 != 0.f)
+                                atomicAdd(reinterpret_cast<float2*>(dst), make_float2(a0, a1));
+                        } else {
+                            if (c < P.n_sem && a0 != 0.f) atomicAdd(dst, a0);
+                            if (c + 1 < P.n_sem && a1 != 0.f) atomicAdd(dst + 1, a1);
                         }
                     }
                 }
