@@ -160,7 +160,7 @@ typedef struct {
     int32_t sort_passes;    /* 8-bit radix passes over the used key bits */
     int32_t reserved;
     size_t ws_bytes;
-    size_t off[16];         /* internal region offsets */
+    size_t off[20];         /* internal region offsets */
     unigs_config cfg;
 } unigs_plan;
 

@@ -71,7 +71,7 @@ class unigs_plan(Structure):
                 ("tile_offset", c_int32 * (UNIGS_MAX_CAMS + 1)),
                 ("pixel_offset", c_int64 * (UNIGS_MAX_CAMS + 1)),
                 ("sort_passes", c_int32), ("reserved", c_int32), ("ws_bytes", c_size_t),
-                ("off", c_size_t * 16), ("cfg", unigs_config)]
+                ("off", c_size_t * 20), ("cfg", unigs_config)]
 
 
 _lib = None

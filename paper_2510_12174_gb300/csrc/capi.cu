@@ -138,6 +138,8 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     sizes[OFF_RANGES] = sizeof(uint2) * (size_t)tiles;
     sizes[OFF_GREC] = sizeof(float) * GREC_FLOATS * (size_t)total;
     sizes[OFF_CULL] = sizeof(float) * CULL_FLOATS * (size_t)total;
+    // float32 copy of bfloat16 semantic rows, refreshed by every preprocess
+    sizes[OFF_SEM32] = g->feat_dtype ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
     size_t off = 0;
     for (int r = 0; r < OFF_END; ++r) {
         plan->off[r] = off;
@@ -251,7 +253,12 @@ int32_t unigs_launches_per_step(const unigs_plan* plan) {
     if (!plan) return 0;
     const int per_pass = 1 + 3 + 1;
     const int bin = 3 + 1 + per_pass * plan->sort_passes + 1;
-    return 2 /*preprocess*/ + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ + 2 /*bwd*/;
+    int conv = 0;
+    if (plan->feat_dtype && plan->n_sem > 0 && plan->n > 0) {
+        const int64_t cnt = plan->n * (int64_t)plan->n_sem;
+        conv = (cnt / 2 > 0 ? 1 : 0) + (int)(cnt & 1);
+    }
+    return 2 /*preprocess*/ + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ + 2 /*bwd*/;
 }
 
 const char* unigs_status_string(unigs_status s) {

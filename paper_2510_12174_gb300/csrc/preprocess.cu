@@ -395,6 +395,19 @@ __global__ void init_kernel(CamTable tab, int n_cams, CamTable* __restrict__ dst
     }
 }
 
+__global__ void sem_tail_kernel(const __nv_bfloat16* __restrict__ src, float* __restrict__ dst) {
+    *dst = __bfloat162float(*src);
+}
+
+// bfloat16 semantic rows -> float32 copy in the workspace (exact), so the
+// composite kernels stage and blend float32 rows only.
+__global__ void __launch_bounds__(256)
+    sem_to_f32_kernel(const __nv_bfloat162* __restrict__ src, float2* __restrict__ dst, int64_t n2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __bfloat1622float2(src[i]);
+}
+
 int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTable& tab,
                       void* ws, cudaStream_t st) {
     init_kernel<<<1, UNIGS_MAX_CAMS, 0, st>>>(tab, p.n_cams, ws_ptr<CamTable>(ws, p, OFF_CAM),
@@ -410,6 +423,26 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
             ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
             ws_ptr<float>(ws, p, OFF_CULL));
         ++launches;
+    }
+    if (p.feat_dtype && p.n_sem > 0 && p.n > 0) {
+        // n * n_sem is even whenever n_sem is (rows of 2-element pairs); an odd
+        // count leaves the last element to a one-element tail launch
+        const int64_t cnt = p.n * (int64_t)p.n_sem;
+        const int64_t n2 = cnt / 2;
+        float* dst = ws_ptr<float>(ws, p, OFF_SEM32);
+        if (n2 > 0) {
+            const int64_t blocks = (n2 + 255) / 256;
+            const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+            sem_to_f32_kernel<<<grid, 256, 0, st>>>(
+                reinterpret_cast<const __nv_bfloat162*>(g.sem), reinterpret_cast<float2*>(dst), n2);
+            ++launches;
+        }
+        if (cnt & 1) {
+            // odd total: convert the last element with a one-thread launch
+            sem_tail_kernel<<<1, 1, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(g.sem) + cnt - 1,
+                                             dst + cnt - 1);
+            ++launches;
+        }
     }
     return launches;
 }

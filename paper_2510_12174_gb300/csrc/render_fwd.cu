@@ -275,13 +275,11 @@ int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
     P.alpha_max = p.cfg.alpha_max;
     P.T_min = p.cfg.T_min;
     P.center_depth = (p.cfg.flags & UNIGS_FLAG_CENTER_DEPTH) ? 1 : 0;
-    const size_t esz = p.feat_dtype ? 2 : 4;
-    P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * esz) % 16 == 0) &&
-                 ((reinterpret_cast<uintptr_t>(g.sem) & 15) == 0);
-    if (p.feat_dtype)
-        launch_fwd_ft<__nv_bfloat16>(P, p.n_tiles, st);
-    else
-        launch_fwd_ft<float>(P, p.n_tiles, st);
+    // bfloat16 logits are read from their float32 copy (made by the preprocess)
+    if (p.feat_dtype) P.sem = ws_ptr<float>(ws, p, OFF_SEM32);
+    P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * 4) % 16 == 0) &&
+                 ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
+    launch_fwd_ft<float>(P, p.n_tiles, st);
     return 1;
 }
 

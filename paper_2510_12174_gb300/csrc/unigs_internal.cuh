@@ -101,7 +101,7 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 enum {
     OFF_HDR = 0, OFF_CAM, OFF_REC, OFF_RECT, OFF_TOUCH, OFF_OFFS, OFF_ZBITS,
     OFF_SCAN, OFF_KEYS0, OFF_KEYS1, OFF_VALS0, OFF_VALS1, OFF_HIST, OFF_RANGES,
-    OFF_GREC, OFF_CULL, OFF_END
+    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_END
 };
 
 // Per-(camera, Gaussian) record of the opacity-aware tile test (8 floats):
