@@ -31,7 +31,8 @@ PARAM_KEYS = ("mean", "quat", "scale", "opacity", "kfac", "sh", "sem")
 
 def render(scene, cams, requires_grad: bool = False, binning=None,
            tiles: Optional[Sequence[Sequence[int]]] = None,
-           bands: Optional[Bands] = None, with_normal_d: bool = True):
+           bands: Optional[Bands] = None, with_normal_d: bool = True,
+           center_depth: bool = False):
     """Forward over all cameras.  Returns (params, per-camera outputs, binning)."""
     if binning is None:
         binning = bin_cameras_fast(scene, cams)
@@ -42,7 +43,8 @@ def render(scene, cams, requires_grad: bool = False, binning=None,
         for k, cam in enumerate(cams):
             prep = preprocess(params, cam)
             r = render_camera(prep, cam, binning, k,
-                              tiles=None if tiles is None else tiles[k], bands=bands)
+                              tiles=None if tiles is None else tiles[k], bands=bands,
+                              center_depth=center_depth)
             if with_normal_d:
                 nd = depth_to_normal(r["depth"], cam)
                 r["normal_d"] = nd["normal"]
@@ -53,7 +55,7 @@ def render(scene, cams, requires_grad: bool = False, binning=None,
 
 
 def render_and_grad(scene, cams, upstream: Dict[str, List[np.ndarray]],
-                    binning=None, bands: Optional[Bands] = None):
+                    binning=None, bands: Optional[Bands] = None, center_depth: bool = False):
     """Forward plus exact gradients of L = sum_c <output_c, upstream_c>.
 
     ``upstream`` maps rgb, depth, normal_g, kmap, logits, normal_d to per-camera
@@ -61,7 +63,7 @@ def render_and_grad(scene, cams, upstream: Dict[str, List[np.ndarray]],
     grads keyed like the Gaussian parameters.
     """
     params, outs, binning = render(scene, cams, requires_grad=True, binning=binning,
-                                   bands=bands)
+                                   bands=bands, center_depth=center_depth)
     loss = torch.zeros((), dtype=torch.float64)
     name = {"rgb": "rgb", "depth": "depth", "normal_g": "normal", "kmap": "kmap",
             "logits": "logits", "normal_d": "normal_d"}

@@ -209,14 +209,17 @@ class Bands:
 
 
 def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
-                   bands: Optional[Bands] = None, frozen=None) -> Dict[str, torch.Tensor]:
+                   bands: Optional[Bands] = None, frozen=None,
+                   center_depth: bool = False) -> Dict[str, torch.Tensor]:
     """Alg. 2 for the pixels ``uv`` [P,2] over the ordered list ``ids`` [L].
 
     ``frozen`` (the ``decisions`` entry of an earlier call on the same pixels
     and list) replays that call's discrete decisions - alpha skip, stop,
     ray hit and camera-inside - so that the result is a smooth function of
     the parameters (used for finite differences of the almost-everywhere
-    derivative)."""
+    derivative).  ``center_depth`` blends the camera-frame depth of each
+    Gaussian centre instead of the ray-ellipsoid midpoint (the centre-depth
+    ablation of Tab. 6)."""
     P = uv.shape[0]
     L = ids.numel()
     C = prep.sem.shape[1]
@@ -258,6 +261,8 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
         prep.R[ids], prep.s[ids], prep.v_s[ids], d, zc,
         frozen="return" if frozen is None else frozen[2])
 
+    if center_depth:
+        depth = prep.z[ids][None, :].expand_as(depth)
     rgb = w @ prep.rgb[ids]
     out = dict(
         rgb=rgb,
@@ -297,7 +302,8 @@ def tile_pixels(cam, tile_id_local: int, tile: int = 16):
 
 def render_camera(prep: Prep, cam, binning, cam_index: int,
                   tiles: Optional[Sequence[int]] = None,
-                  bands: Optional[Bands] = None) -> Dict[str, torch.Tensor]:
+                  bands: Optional[Bands] = None,
+                  center_depth: bool = False) -> Dict[str, torch.Tensor]:
     """Composite every pixel of the listed local tiles (default: all) of one camera.
 
     Returns full-size planar images [C,H,W] (pixels of unlisted tiles are 0).
@@ -320,7 +326,7 @@ def render_camera(prep: Prep, cam, binning, cam_index: int,
         ids = torch.as_tensor(vals[s0:s1].astype(np.int64))
         uu, vv = tile_pixels(cam, t)
         uv = torch.as_tensor(np.stack([uu, vv], 1), dtype=F64)
-        r = composite_tile(prep, ids, uv, cam, bands)
+        r = composite_tile(prep, ids, uv, cam, bands, center_depth=center_depth)
         vi = torch.as_tensor(vv)
         ui = torch.as_tensor(uu)
         for k in outs:

@@ -170,6 +170,24 @@ def test_backward_parity_bf16_features():
     check_grad_errors(_grad_case(sc, cams), norm=3e-4)
 
 
+def test_center_depth_ablation_forward_and_backward():
+    """UNIGS_FLAG_CENTER_DEPTH (the centre-depth ablation of Tab. 6) against
+    the oracle in the same mode: forward depth and the gradients."""
+    sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=8, seed=25)
+    r, out = _render(sc, cams, center_depth=True)
+    _, ref, _ = oracle.render(sc, cams, with_normal_d=False, center_depth=True)
+    e = forward_errors(r, out, ref, sc.n_sem)
+    assert e["depth"] < TOL_REL and e["rgb"] < TOL_ABS
+    up = scenes.upstream_grads(cams, sc.n_sem, seed=26)
+    up = masked_upstream(up, [rf["amb_grad"].numpy() for rf in ref])
+    up["normal_d"] = [np.zeros_like(x) for x in up["normal_d"]]
+    _, gref, _ = oracle.render_and_grad(sc, cams, up, center_depth=True)
+    fu = flat_upstream(up)
+    grads = r.backward(out, {k: fu[k] for k in fu if k != "normal_d"})
+    torch.cuda.synchronize()
+    check_grad_errors(grad_errors(grads, gref))
+
+
 def test_capacity_overflow_reports_and_recovers():
     sc, cams = scenes.small_room(n=4000, seed=14)
     ds = rz.DeviceScene.from_scene(sc)

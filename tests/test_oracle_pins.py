@@ -449,6 +449,23 @@ def test_composite_invariants():
     assert torch.abs(outs2[0]["logits"] - 2.5 * r["logits"]).max() < 1e-12
 
 
+def test_center_depth_ablation_blends_centre_z():
+    """Centre-depth mode (Tab. 6 ablation): D = sum_i w_i z_i with z_i the
+    camera-frame depth of the centre and the weights of Alg. 2.  Pinned through
+    the K channel: with k_i := z_i, Eq. t_render gives the same sum."""
+    sc, cams = scenes.small_room(n=3000, width=40, height=32, n_sem=2, seed=23)
+    cam = cams[0]
+    _, a, b = oracle.render(sc, cams, with_normal_d=False)
+    _, c, _ = oracle.render(sc, cams, with_normal_d=False, binning=b, center_depth=True)
+    assert torch.equal(a[0]["rgb"], c[0]["rgb"]) and torch.equal(a[0]["T"], c[0]["T"])
+    sc1 = scenes.Scene(**{**sc.__dict__})
+    pc = sc.mean.astype(np.float64).T @ cam.R_wc.astype(np.float64).T + cam.t_wc.astype(np.float64)
+    sc1.kfac = pc[:, 2].copy()
+    _, k1, _ = oracle.render(sc1, cams, with_normal_d=False, binning=b)
+    assert torch.abs(c[0]["depth"] - k1[0]["kmap"]).max() < 1e-12
+    assert torch.abs(c[0]["depth"] - a[0]["depth"]).max() > 1e-4  # the modes differ
+
+
 # ------------------------------------------------- normal from depth
 def _plane_depth(cam, n, d0):
     """Depth map of the world plane n.X = d0 seen by ``cam``."""
