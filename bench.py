@@ -150,11 +150,13 @@ def run_ours(args):
 
     # ------------------------------------------------ batched (BF16, graph)
     ds = rz.DeviceScene.from_scene(sc, device=dev, feat_bf16=True)
-    r = rz.Renderer(ds, cams)
+    cfg = abi.unigs_config_default()
+    cfg.batch, cfg.ctas_per_sm = args.batch, args.ctas
+    r = rz.Renderer(ds, cams, cfg=cfg)
     out = r.forward()                      # sizes the capacity (one read-back)
     torch.cuda.synchronize()
     cap = int(r.last_instances * 1.15) + 65536
-    r = rz.Renderer(ds, cams, capacity=cap)
+    r = rz.Renderer(ds, cams, cfg=cfg, capacity=cap)
     out = r.alloc_outputs()
     grads = r.alloc_grads()
     gbuf = torch.empty(r.n_pixels, device=dev)
@@ -303,7 +305,9 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "gaussians": args.n_gauss, "views_per_step": N_VIEWS,
                    "resolution": "1280x720", "n_sem": n_sem, "features": "bf16 storage",
                    "path": "batched, one CUDA graph per step", "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (no flush)"},
+                   "l2": "inputs larger than L2 (no flush)",
+                   "launch_shape": {"batch": int(r.cfg.batch) or 32,
+                                    "ctas_per_sm": int(r.cfg.ctas_per_sm) or 2}},
         "per_view": pv,
         "stage_ms": {"preprocess+bin_sort": stage_ms[0], "render_fwd+normal_d": stage_ms[1],
                      "depth_normal_bwd": stage_ms[2], "render_bwd": stage_ms[3]},
@@ -406,6 +410,10 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=12)
     ap.add_argument("--skip-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, choices=[0, 16, 32, 64],
+                    help="Gaussians staged per batch by the composites (0: library default)")
+    ap.add_argument("--ctas", type=int, default=0,
+                    help="persistent composite CTAs per SM (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -134,7 +134,9 @@ typedef struct {
 /* Compositing and normal-from-depth settings.  unigs_config_default() fills
  * alpha_min 1/255, alpha_max 0.99, T_min 1e-4, lowpass 0.3 (the 3DGS values
  * the paper keeps, Sec. 3.4), step1 1, step2 2, lambda 0.5 (Alg. 1; the
- * paper does not print its values). */
+ * paper does not print its values), and the launch shape batch 32, 2 CTAs
+ * per SM (the results do not depend on the launch shape beyond float32
+ * atomic summation order). */
 typedef struct {
     float alpha_min, alpha_max, T_min, lowpass;
     int32_t step1, step2; /* 1..4 */
@@ -142,6 +144,10 @@ typedef struct {
     uint32_t flags;       /* bit 0: UNIGS_FLAG_CENTER_DEPTH (depth of the
                              Gaussian centre instead of the midpoint, the
                              ablation of Tab. 6) */
+    int32_t batch;        /* Gaussians staged per batch by the composite
+                             kernels: 16, 32 or 64 (0 = 32) */
+    int32_t ctas_per_sm;  /* persistent CTAs per SM of the composite kernels,
+                             1..8 (0 = 2) */
 } unigs_config;
 
 #define UNIGS_FLAG_CENTER_DEPTH 1u

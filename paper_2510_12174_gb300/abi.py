@@ -61,7 +61,8 @@ class unigs_param_grads(Structure):
 class unigs_config(Structure):
     _fields_ = [("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
                 ("lowpass", c_float), ("step1", c_int32), ("step2", c_int32),
-                ("lambda_", c_float), ("flags", c_uint32)]
+                ("lambda_", c_float), ("flags", c_uint32), ("batch", c_int32),
+                ("ctas_per_sm", c_int32)]
 
 
 class unigs_plan(Structure):

@@ -302,6 +302,34 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Tile schedule of the persistent composite kernels: global tile ids ordered
+// by descending list length, bucketed by floor(log2(length)) (one block;
+// the order inside a bucket is arbitrary and affects scheduling only).
+__global__ void __launch_bounds__(1024)
+    tile_order_kernel(const uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[33];
+    __shared__ uint32_t base[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&cnt[__clz(r.y - r.x)], 1u);  // longer lists -> fewer leading zeros
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < 33; ++b) {
+            base[b] = run;
+            run += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&base[__clz(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
+}
+
 int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long long* kout,
                uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
                int shift, int nb, cudaStream_t st) {
@@ -317,7 +345,11 @@ int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
     uint2* ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
     int launches = 0;
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)p.n_tiles, st);
-    if (total == 0 || p.capacity == 0) return launches;
+    if (total == 0 || p.capacity == 0) {
+        // no instances: every tile is empty, the schedule is still needed
+        tile_order_kernel<<<1, 1024, 0, st>>>(ranges, p.n_tiles, ws_ptr<uint32_t>(ws, p, OFF_ORDER));
+        return launches + 1;
+    }
     uint32_t* touched = ws_ptr<uint32_t>(ws, p, OFF_TOUCH);
     uint32_t* offs = ws_ptr<uint32_t>(ws, p, OFF_OFFS);
     uint32_t* scan_tmp = ws_ptr<uint32_t>(ws, p, OFF_SCAN);
@@ -351,6 +383,8 @@ int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
         ranges_kernel<<<grid, 256, 0, st>>>(keys[fin], hdr, ranges);
         ++launches;
     }
+    tile_order_kernel<<<1, 1024, 0, st>>>(ranges, p.n_tiles, ws_ptr<uint32_t>(ws, p, OFF_ORDER));
+    ++launches;
     return launches;
 }
 

@@ -5,6 +5,21 @@
 
 using namespace unigs;
 
+namespace unigs {
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+}  // namespace unigs
+
 namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -70,6 +85,8 @@ void unigs_config_default(unigs_config* cfg) {
     cfg->step2 = 2;
     cfg->lambda = 0.5f;
     cfg->flags = 0;
+    cfg->batch = 0;
+    cfg->ctas_per_sm = 0;
 }
 
 unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const unigs_camera* cams,
@@ -89,6 +106,10 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     if (plan->cfg.step1 < 1 || plan->cfg.step1 > 4 || plan->cfg.step2 < 1 || plan->cfg.step2 > 4)
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.flags & ~UNIGS_FLAG_CENTER_DEPTH) return UNIGS_ERR_INVALID_ARG;
+    if (plan->cfg.batch != 0 && plan->cfg.batch != 16 && plan->cfg.batch != 32 &&
+        plan->cfg.batch != 64)
+        return UNIGS_ERR_INVALID_ARG;
+    if (plan->cfg.ctas_per_sm < 0 || plan->cfg.ctas_per_sm > 8) return UNIGS_ERR_INVALID_ARG;
     plan->n = g->n;
     plan->n_cams = n_cams;
     plan->n_sem = g->n_sem;
@@ -140,6 +161,7 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     sizes[OFF_CULL] = sizeof(float) * CULL_FLOATS * (size_t)total;
     // float32 copy of bfloat16 semantic rows, refreshed by every preprocess
     sizes[OFF_SEM32] = g->feat_dtype ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
+    sizes[OFF_ORDER] = sizeof(uint32_t) * (size_t)tiles;
     size_t off = 0;
     for (int r = 0; r < OFF_END; ++r) {
         plan->off[r] = off;
@@ -252,7 +274,7 @@ unigs_status unigs_stats_poll(const unigs_plan* plan, const void* ws, int64_t* p
 int32_t unigs_launches_per_step(const unigs_plan* plan) {
     if (!plan) return 0;
     const int per_pass = 1 + 3 + 1;
-    const int bin = 3 + 1 + per_pass * plan->sort_passes + 1;
+    const int bin = 3 + 1 + per_pass * plan->sort_passes + 1 + 1 /*tile order*/;
     int conv = 0;
     if (plan->feat_dtype && plan->n_sem > 0 && plan->n > 0) {
         const int64_t cnt = plan->n * (int64_t)plan->n_sem;

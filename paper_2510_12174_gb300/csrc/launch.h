@@ -28,6 +28,9 @@ int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long
                uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
                int shift, int nb, cudaStream_t st);
 
+// Number of SMs of the current device (queried once per device).
+int sm_count();
+
 // Index of the buffer (0/1) that holds the sorted keys/values after the sort.
 inline int sorted_buffer(const unigs_plan& p) { return p.sort_passes & 1; }
 

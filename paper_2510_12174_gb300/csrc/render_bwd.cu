@@ -25,7 +25,6 @@
 
 namespace unigs {
 
-constexpr int BBATCH = 32;
 constexpr uint32_t BWAIT_LIMIT = 1u << 22;
 
 struct BwdParams {
@@ -33,10 +32,13 @@ struct BwdParams {
     int n_cams;
     int n_sem;
     int64_t n;
+    int64_t n_tiles;
     const float* rec;
-    const void* sem;
+    const float* sem;          // float32 rows (a float32 copy for bfloat16 storage)
     const uint32_t* vals;
     const uint2* ranges;
+    const uint32_t* order;     // global tile ids, longest list first
+    uint32_t* work;            // tile counter
     WsHeader* hdr;
     const float* T_final;
     const uint32_t* n_contrib;
@@ -48,16 +50,17 @@ struct BwdParams {
     int sem_bulk;
 };
 
-template <int NS, typename FT>
+template <int NS, int B>
 struct BwdSmem {
     static constexpr int GOP = NS + 4;  // padded pitch: row reads and column gathers
                                         // both avoid bank conflicts
-    float rec[2][BBATCH][REC_FLOATS];
-    FT sem[2][BBATCH][NS];
+    float rec[2][B][REC_FLOATS];
+    float sem[2][B][NS];
     float gO[TILE_PIX][GOP];            // dL/dlogits of the tile's pixels, by thread
-    uint32_t ids[2][BBATCH];
+    uint32_t ids[2][B];
     uint64_t bar[2];
     uint32_t max_last;
+    int tile;
 };
 
 // dot(gO row, semantic row) with 16-byte shared-memory loads.
@@ -72,49 +75,28 @@ __device__ __forceinline__ float sem_dot(const float* go, const float* row) {
     }
     return acc;
 }
-template <int NS>
-__device__ __forceinline__ float sem_dot(const float* go, const __nv_bfloat16* row) {
-    float acc = 0.f;
-#pragma unroll
-    for (int c = 0; c < NS / 8; ++c) {
-        const float4 a0 = reinterpret_cast<const float4*>(go)[2 * c];
-        const float4 a1 = reinterpret_cast<const float4*>(go)[2 * c + 1];
-        const uint4 bb = reinterpret_cast<const uint4*>(row)[c];
-        const float2 b0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.x));
-        const float2 b1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.y));
-        const float2 b2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.z));
-        const float2 b3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bb.w));
-        acc = fmaf(a0.x, b0.x, fmaf(a0.y, b0.y, fmaf(a0.z, b1.x, fmaf(a0.w, b1.y, acc))));
-        acc = fmaf(a1.x, b2.x, fmaf(a1.y, b2.y, fmaf(a1.z, b3.x, fmaf(a1.w, b3.y, acc))));
-    }
-    return acc;
-}
-
-template <int NS, typename FT>
-__device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, FT>& S, int buf,
+template <int NS, int B>
+__device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, B>& S, int buf,
                                           uint32_t first, int count, int cam) {
     const int lane = threadIdx.x & 31;
-    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(FT));
+    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(float));
     const uint32_t per = REC_FLOATS * 4 + (P.sem_bulk ? row_bytes : 0u);
     if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], per * (uint32_t)count);
     __syncwarp();
-    if (lane < count) {
-        const uint32_t g = P.vals[first + lane];
-        S.ids[buf][lane] = g;
+    for (int i = lane; i < count; i += 32) {
+        const uint32_t g = P.vals[first + i];
+        S.ids[buf][i] = g;
         const size_t r = (size_t)cam * (size_t)P.n + g;
-        bulk_g2s(&S.rec[buf][lane][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
+        bulk_g2s(&S.rec[buf][i][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
         if (P.n_sem > 0) {
-            const FT* src = reinterpret_cast<const FT*>(P.sem) + (size_t)g * P.n_sem;
+            const float* src = P.sem + (size_t)g * P.n_sem;
             if (P.sem_bulk)
-                bulk_g2s(&S.sem[buf][lane][0], src, row_bytes, &S.bar[buf]);
+                bulk_g2s(&S.sem[buf][i][0], src, row_bytes, &S.bar[buf]);
             else
-                for (int c = 0; c < P.n_sem; ++c) S.sem[buf][lane][c] = src[c];
+                for (int c = 0; c < P.n_sem; ++c) S.sem[buf][i][c] = src[c];
         }
     }
 }
-
-__device__ __forceinline__ float to_f(float x) { return x; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 __device__ __forceinline__ void cross_acc(const float* a, const float* b, float* c) {
     c[0] += a[1] * b[2] - a[2] * b[1];
@@ -122,86 +104,96 @@ __device__ __forceinline__ void cross_acc(const float* a, const float* b, float*
     c[2] += a[0] * b[1] - a[1] * b[0];
 }
 
-template <int NS, typename FT>
+template <int NS, int B>
 __global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    BwdSmem<NS, FT>& S = *reinterpret_cast<BwdSmem<NS, FT>*>(smem_raw);
+    BwdSmem<NS, B>& S = *reinterpret_cast<BwdSmem<NS, B>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t gtile = blockIdx.x;
-    int cam_idx;
-    const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
-    const int64_t ltile = gtile - cam.tile_off;
-    const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
-    int lx, ly;
-    tile_pixel(tid, &lx, &ly);
-    const int u = tx * TILE + lx, v = ty * TILE + ly;
-    // the warp's 8x4 pixel block, for the per-warp bounding-box skip
-    const float bx0 = (float)(tx * TILE + ((tid >> 5) & 1) * 8);
-    const float by0 = (float)(ty * TILE + (tid >> 6) * 4);
-    const bool inside = u < cam.width && v < cam.height;
-    const float uf = (float)u, vf = (float)v;
-    const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
-    const int W = cam.width;
-    const int64_t HW = (int64_t)cam.height * W;
-    const int64_t pix = cam.pix_off;
-    const int64_t idx = (int64_t)v * W + u;
 
-    float T = 1.f;
-    uint32_t last = 0;
-    float g_rgb[3] = {0.f, 0.f, 0.f}, g_D = 0.f, g_N[3] = {0.f, 0.f, 0.f}, g_K = 0.f;
-    // upstream logit gradients of this pixel -> shared memory row tid (zero
-    // padded), read by this thread for G_i and by the warp's channel gather
-#pragma unroll 8
-    for (int c = 0; c < BwdSmem<NS, FT>::GOP; ++c)
-        S.gO[tid][c] = (inside && P.go.logits && c < P.n_sem)
-                           ? P.go.logits[pix * (int64_t)P.n_sem + c * HW + idx] : 0.f;
-    if (inside) {
-        T = P.T_final[pix + idx];
-        last = P.n_contrib[pix + idx];
-        if (P.go.rgb)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) g_rgb[c] = P.go.rgb[pix * 3 + c * HW + idx];
-        if (P.go.depth) g_D = P.go.depth[pix + idx];
-        if (P.go.normal_g)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) g_N[c] = P.go.normal_g[pix * 3 + c * HW + idx];
-        if (P.go.kmap) g_K = P.go.kmap[pix + idx];
-    }
-
+    // once per CTA: init barriers, zero the semantic padding
     if (tid == 0) {
-        S.max_last = 0;
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
     }
-    for (int j = tid; j < 2 * BBATCH * NS; j += 256) (&S.sem[0][0][0])[j] = FT(0.f);
+    for (int j = tid; j < 2 * B * NS; j += 256) (&S.sem[0][0][0])[j] = 0.f;
     __syncthreads();
-    if (last) atomicMax(&S.max_last, last);
-    __syncthreads();
-    const int n_items = (int)S.max_last;
-    const int n_batches = (n_items + BBATCH - 1) / BBATCH;
-    const uint2 range = P.ranges[gtile];
-    if (n_batches == 0) return;
-    if (warp == 0)
-        bwd_issue<NS, FT>(P, S, 0, range.x + (n_batches - 1) * BBATCH,
-                          min(BBATCH, n_items - (n_batches - 1) * BBATCH), cam_idx);
-    // ids and unaligned semantic rows are staged with plain stores: make the
-    // first batch visible (later batches are ordered by the end-of-batch barrier)
-    __syncthreads();
-
-    float Sacc = 0.f;  // sum over already processed (later) Gaussians of w_j G_j
+    uint32_t loads[2] = {0u, 0u};  // completed loads per buffer (uniform)
     bool timed_out = false;
-    for (int it = 0; it < n_batches; ++it) {
-        const int b = n_batches - 1 - it;
-        const int buf = it & 1;
-        if (warp == 0 && b > 0)
-            bwd_issue<NS, FT>(P, S, buf ^ 1, range.x + (b - 1) * BBATCH, BBATCH, cam_idx);
-        if (!mbar_wait_bounded(&S.bar[buf], (uint32_t)(it >> 1) & 1u, BWAIT_LIMIT))
-            timed_out = true;
-        const int count = min(BBATCH, n_items - b * BBATCH);
-        if (!__all_sync(0xffffffffu, timed_out)) {
+
+    for (;;) {
+        if (tid == 0) {
+            S.tile = (int)atomicAdd(P.work, 1u);
+            S.max_last = 0;
+        }
+        __syncthreads();
+        const int64_t t = S.tile;
+        if (t >= P.n_tiles) break;
+        const int64_t gtile = P.order[t];
+        int cam_idx;
+        const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
+        const int64_t ltile = gtile - cam.tile_off;
+        const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
+        int lx, ly;
+        tile_pixel(tid, &lx, &ly);
+        const int u = tx * TILE + lx, v = ty * TILE + ly;
+        // the warp's 8x4 pixel block, for the per-warp bounding-box skip
+        const float bx0 = (float)(tx * TILE + (warp & 1) * 8);
+        const float by0 = (float)(ty * TILE + (warp >> 1) * 4);
+        const bool inside = u < cam.width && v < cam.height;
+        const float uf = (float)u, vf = (float)v;
+        const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
+        const int W = cam.width;
+        const int64_t HW = (int64_t)cam.height * W;
+        const int64_t pix = cam.pix_off;
+        const int64_t idx = (int64_t)v * W + u;
+
+        float T = 1.f;
+        uint32_t last = 0;
+        float g_rgb[3] = {0.f, 0.f, 0.f}, g_D = 0.f, g_N[3] = {0.f, 0.f, 0.f}, g_K = 0.f;
+        // upstream logit gradients of this pixel -> shared memory row tid (zero
+        // padded), read by this thread for G_i and by the warp's channel gather
+#pragma unroll 8
+        for (int c = 0; c < BwdSmem<NS, B>::GOP; ++c)
+            S.gO[tid][c] = (inside && P.go.logits && c < P.n_sem)
+                               ? P.go.logits[pix * (int64_t)P.n_sem + c * HW + idx] : 0.f;
+        if (inside) {
+            T = P.T_final[pix + idx];
+            last = P.n_contrib[pix + idx];
+            if (P.go.rgb)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g_rgb[c] = P.go.rgb[pix * 3 + c * HW + idx];
+            if (P.go.depth) g_D = P.go.depth[pix + idx];
+            if (P.go.normal_g)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g_N[c] = P.go.normal_g[pix * 3 + c * HW + idx];
+            if (P.go.kmap) g_K = P.go.kmap[pix + idx];
+        }
+        if (last) atomicMax(&S.max_last, last);
+        __syncthreads();
+        const int n_items = (int)S.max_last;
+        const int n_batches = (n_items + B - 1) / B;
+        const uint2 range = P.ranges[gtile];
+        if (warp == 0 && n_batches > 0)
+            bwd_issue<NS, B>(P, S, 0, range.x + (n_batches - 1) * B,
+                             min(B, n_items - (n_batches - 1) * B), cam_idx);
+        // ids and unaligned semantic rows are staged with plain stores: make
+        // the first batch visible (later batches are ordered by the
+        // end-of-batch barrier)
+        __syncthreads();
+
+        float Sacc = 0.f;  // sum over already processed (later) Gaussians of w_j G_j
+        for (int it = 0; it < n_batches; ++it) {
+            const int b = n_batches - 1 - it;
+            const int buf = it & 1;
+            if (warp == 0 && b > 0)
+                bwd_issue<NS, B>(P, S, buf ^ 1, range.x + (b - 1) * B, B, cam_idx);
+            if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, BWAIT_LIMIT)) timed_out = true;
+            ++loads[buf];
+            const int count = min(B, n_items - b * B);
+            if (!__all_sync(0xffffffffu, timed_out)) {
             for (int j = count - 1; j >= 0; --j) {
-                const uint32_t pos = (uint32_t)(b * BBATCH + j);
+                const uint32_t pos = (uint32_t)(b * B + j);
                 const float* rc = &S.rec[buf][j][0];
                 if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
                 float gv[32];
@@ -346,8 +338,11 @@ __global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
                     }
                 }
             }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        // a bounded wait that gave up ends the CTA (uniformly)
+        if (__syncthreads_or(timed_out)) break;
     }
     if (timed_out && lane == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
 }
@@ -559,28 +554,28 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
     }
 }
 
-template <int NS, typename FT>
-static void launch_bwd_t(const BwdParams& P, int64_t n_tiles, cudaStream_t st) {
-    const size_t smem = sizeof(BwdSmem<NS, FT>);
+template <int NS, int B>
+static void launch_bwd_t(const BwdParams& P, int grid, cudaStream_t st) {
+    const size_t smem = sizeof(BwdSmem<NS, B>);
     static bool attr_set = false;  // host-side, set once per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(render_bwd_kernel<NS, FT>,
+        cudaFuncSetAttribute(render_bwd_kernel<NS, B>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    render_bwd_kernel<NS, FT><<<(unsigned)n_tiles, 256, smem, st>>>(P);
+    render_bwd_kernel<NS, B><<<grid, 256, smem, st>>>(P);
 }
 
-template <typename FT>
-static void launch_bwd_ft(const BwdParams& P, int64_t n_tiles, cudaStream_t st) {
+template <int B>
+static void launch_bwd_b(const BwdParams& P, int grid, cudaStream_t st) {
     if (P.n_sem <= 8)
-        launch_bwd_t<8, FT>(P, n_tiles, st);
+        launch_bwd_t<8, B>(P, grid, st);
     else if (P.n_sem <= 16)
-        launch_bwd_t<16, FT>(P, n_tiles, st);
+        launch_bwd_t<16, B>(P, grid, st);
     else if (P.n_sem <= 32)
-        launch_bwd_t<32, FT>(P, n_tiles, st);
+        launch_bwd_t<32, B>(P, grid, st);
     else
-        launch_bwd_t<64, FT>(P, n_tiles, st);
+        launch_bwd_t<64, B>(P, grid, st);
 }
 
 int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
@@ -597,12 +592,17 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         P.n_cams = p.n_cams;
         P.n_sem = p.n_sem;
         P.n = p.n;
+        P.n_tiles = p.n_tiles;
         P.rec = ws_ptr<float>(ws, p, OFF_REC);
-        P.sem = g.sem;
+        // bfloat16 logits are read from their float32 copy (made by the preprocess)
+        P.sem = p.feat_dtype ? ws_ptr<float>(ws, p, OFF_SEM32) : static_cast<const float*>(g.sem);
         P.vals = sorted_buffer(p) ? ws_ptr<uint32_t>(ws, p, OFF_VALS1)
                                   : ws_ptr<uint32_t>(ws, p, OFF_VALS0);
         P.ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
-        P.hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+        P.order = ws_ptr<uint32_t>(ws, p, OFF_ORDER);
+        WsHeader* hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+        P.work = &hdr->work_bwd;
+        P.hdr = hdr;
         P.T_final = fwd.T_final;
         P.n_contrib = fwd.n_contrib;
         P.go = go;
@@ -611,11 +611,17 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         P.alpha_min = p.cfg.alpha_min;
         P.alpha_max = p.cfg.alpha_max;
         P.center_depth = (p.cfg.flags & UNIGS_FLAG_CENTER_DEPTH) ? 1 : 0;
-        // bfloat16 logits are read from their float32 copy (made by the preprocess)
-        if (p.feat_dtype) P.sem = ws_ptr<float>(ws, p, OFF_SEM32);
         P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * 4) % 16 == 0) &&
                      ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
-        launch_bwd_ft<float>(P, p.n_tiles, st);
+        cudaMemsetAsync(P.work, 0, sizeof(uint32_t), st);
+        const int ctas = p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 2;
+        int64_t grid = (int64_t)sm_count() * ctas;
+        if (grid > p.n_tiles) grid = p.n_tiles;
+        switch (p.cfg.batch) {
+            case 16: launch_bwd_b<16>(P, (int)grid, st); break;
+            case 64: launch_bwd_b<64>(P, (int)grid, st); break;
+            default: launch_bwd_b<32>(P, (int)grid, st); break;
+        }
         ++launches;
     }
     if (p.n > 0) {

@@ -1,5 +1,5 @@
-// Forward composite (Alg. 2): one CTA of 256 threads per 16x16 tile, one
-// pixel per thread.
+// Forward composite (Alg. 2): 256 threads per 16x16 tile, one pixel per
+// thread, persistent CTAs.
 //
 // Per pixel and per Gaussian of the tile's front-to-back list: alpha from the
 // 2D splat, skip below alpha_min, stop before the Gaussian that would bring T
@@ -8,17 +8,22 @@
 // and the logits (Eq. semantic_render) in registers; save T_final and the
 // 1-based list position of the last blended Gaussian for the backward.
 //
-// Staging: the list is walked in batches of BATCH Gaussians.  Warp 0 issues
-// one bulk copy (TMA engine) per Gaussian record (144 B) and per semantic row
+// Scheduling: a fixed grid of CTAs pulls global tile ids from a device work
+// counter in the order of a tile list sorted by descending list length (all
+// cameras of the plan in one launch), so long tiles start first and the tail
+// is short.
+//
+// Staging: the list is walked in batches of B Gaussians.  Warp 0 issues one
+// bulk copy (TMA engine) per Gaussian record (160 B) and per semantic row
 // into a double-buffered shared-memory area completing on an mbarrier, so
-// batch b+1 streams in while batch b is composited.  A warp whose 32 pixels
-// are all finished skips the batch; the CTA leaves when all 256 are.
+// batch b+1 streams in while batch b is composited.  A warp whose 8x4 pixel
+// block lies outside a Gaussian's alpha box, or whose pixels are all
+// finished, skips it; the CTA moves on when all 256 pixels are finished.
 #include "launch.h"
 #include "splat.cuh"
 
 namespace unigs {
 
-constexpr int BATCH = 32;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 struct FwdParams {
@@ -26,10 +31,13 @@ struct FwdParams {
     int n_cams;
     int n_sem;
     int64_t n;
+    int64_t n_tiles;
     const float* rec;
-    const void* sem;
+    const float* sem;          // float32 rows (a float32 copy for bfloat16 storage)
     const uint32_t* vals;
     const uint2* ranges;
+    const uint32_t* order;     // global tile ids, longest list first
+    uint32_t* work;            // tile counter
     WsHeader* hdr;
     unigs_outputs out;
     float alpha_min, alpha_max, T_min;
@@ -37,32 +45,33 @@ struct FwdParams {
     int sem_bulk;  // semantic rows are 16-byte multiples and aligned
 };
 
-template <int NS, typename FT>
+template <int NS, int B>
 struct FwdSmem {
-    float rec[2][BATCH][REC_FLOATS];
-    FT sem[2][BATCH][NS];
+    float rec[2][B][REC_FLOATS];
+    float sem[2][B][NS];
     uint64_t bar[2];
+    int tile;
 };
 
-template <int NS, typename FT>
-__device__ __forceinline__ void issue_batch(const FwdParams& P, FwdSmem<NS, FT>& S, int buf,
+template <int NS, int B>
+__device__ __forceinline__ void issue_batch(const FwdParams& P, FwdSmem<NS, B>& S, int buf,
                                             uint32_t first, int count, int cam) {
     // executed by warp 0 only
     const int lane = threadIdx.x & 31;
-    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(FT));
+    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(float));
     const uint32_t per = REC_FLOATS * 4 + (P.sem_bulk ? row_bytes : 0u);
     if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], per * (uint32_t)count);
     __syncwarp();
-    if (lane < count) {
-        const uint32_t g = P.vals[first + lane];
+    for (int i = lane; i < count; i += 32) {
+        const uint32_t g = P.vals[first + i];
         const size_t r = (size_t)cam * (size_t)P.n + g;
-        bulk_g2s(&S.rec[buf][lane][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
+        bulk_g2s(&S.rec[buf][i][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
         if (P.n_sem > 0) {
-            const FT* src = reinterpret_cast<const FT*>(P.sem) + (size_t)g * P.n_sem;
+            const float* src = P.sem + (size_t)g * P.n_sem;
             if (P.sem_bulk) {
-                bulk_g2s(&S.sem[buf][lane][0], src, row_bytes, &S.bar[buf]);
+                bulk_g2s(&S.sem[buf][i][0], src, row_bytes, &S.bar[buf]);
             } else {
-                for (int c = 0; c < P.n_sem; ++c) S.sem[buf][lane][c] = src[c];
+                for (int c = 0; c < P.n_sem; ++c) S.sem[buf][i][c] = src[c];
             }
         }
     }
@@ -81,123 +90,146 @@ __device__ __forceinline__ void accumulate_row(const float* row, float w, float 
         co[4 * c + 3] = fmaf(w, x.w, co[4 * c + 3]);
     }
 }
-template <int NS>
-__device__ __forceinline__ void accumulate_row(const __nv_bfloat16* row, float w,
-                                               float (&co)[NS]) {
-    const uint4* r8 = reinterpret_cast<const uint4*>(row);
-#pragma unroll
-    for (int c = 0; c < NS / 8; ++c) {
-        const uint4 x = r8[c];
-        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wv[q]));
-            co[8 * c + 2 * q] = fmaf(w, f.x, co[8 * c + 2 * q]);
-            co[8 * c + 2 * q + 1] = fmaf(w, f.y, co[8 * c + 2 * q + 1]);
-        }
-    }
-}
 
-template <int NS, typename FT>
+template <int NS, int B>
 __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    FwdSmem<NS, FT>& S = *reinterpret_cast<FwdSmem<NS, FT>*>(smem_raw);
+    FwdSmem<NS, B>& S = *reinterpret_cast<FwdSmem<NS, B>*>(smem_raw);
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int64_t gtile = blockIdx.x;
-    int cam_idx;
-    const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
-    const int64_t ltile = gtile - cam.tile_off;
-    const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
-    int lx, ly;
-    tile_pixel(tid, &lx, &ly);
-    const int u = tx * TILE + lx, v = ty * TILE + ly;
-    // the warp's 8x4 pixel block, for the per-warp bounding-box skip
-    const float bx0 = (float)(tx * TILE + ((tid >> 5) & 1) * 8);
-    const float by0 = (float)(ty * TILE + (tid >> 6) * 4);
-    const bool inside = u < cam.width && v < cam.height;
-    const float uf = (float)u, vf = (float)v;
-    const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
 
-    const uint2 range = P.ranges[gtile];
-    const int n_items = (int)(range.y - range.x);
-    const int n_batches = (n_items + BATCH - 1) / BATCH;
-
-    // zero the semantic padding once (rows shorter than NS), init barriers
-    for (int j = tid; j < 2 * BATCH * NS; j += 256) (&S.sem[0][0][0])[j] = FT(0.f);
+    // once per CTA: zero the semantic padding (rows shorter than NS), init barriers
+    for (int j = tid; j < 2 * B * NS; j += 256) (&S.sem[0][0][0])[j] = 0.f;
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (warp == 0 && n_batches > 0)
-        issue_batch<NS, FT>(P, S, 0, range.x, min(BATCH, n_items), cam_idx);
-    // rows staged with plain stores (unaligned semantic rows) must be visible
-    // before the first batch is read; later batches are ordered by the
-    // end-of-batch barrier
-    __syncthreads();
-
-    float T = 1.f;
-    float crgb[3] = {0.f, 0.f, 0.f}, cdep = 0.f, cn[3] = {0.f, 0.f, 0.f}, ck = 0.f;
-    float co[NS];
-#pragma unroll
-    for (int c = 0; c < NS; ++c) co[c] = 0.f;
-    uint32_t last = 0;
-    uint32_t n_eval = 0, n_blend = 0;
-    bool done = !inside;
+    // completed loads per buffer (uniform across the CTA): the parity of the
+    // next phase to wait for
+    uint32_t loads[2] = {0u, 0u};
     bool timed_out = false;
+    uint32_t n_eval = 0, n_blend = 0;
 
-    for (int b = 0; b < n_batches; ++b) {
-        const int buf = b & 1;
-        if (warp == 0 && b + 1 < n_batches)
-            issue_batch<NS, FT>(P, S, buf ^ 1, range.x + (b + 1) * BATCH,
-                                min(BATCH, n_items - (b + 1) * BATCH), cam_idx);
-        if (!mbar_wait_bounded(&S.bar[buf], (uint32_t)(b >> 1) & 1u, WAIT_LIMIT)) {
-            timed_out = true;
-        }
-        const int count = min(BATCH, n_items - b * BATCH);
-        const bool skip = __all_sync(0xffffffffu, done || timed_out);
-        if (!skip) {
-            for (int j = 0; j < count; ++j) {
-                const float* rc = &S.rec[buf][j][0];
-                if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
-                if (done) continue;
-                float dx, dy, Gs;
-                const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
-                ++n_eval;
-                if (alpha < P.alpha_min) continue;
-                const float test_T = T * (1.f - alpha);
-                if (test_T < P.T_min) {
-                    done = true;
-                    continue;
+    for (;;) {
+        if (tid == 0) S.tile = (int)atomicAdd(P.work, 1u);
+        __syncthreads();
+        const int64_t t = S.tile;
+        __syncthreads();
+        if (t >= P.n_tiles) break;
+        const int64_t gtile = P.order[t];
+        int cam_idx;
+        const DevCam& cam = cam_of_tile(P.tab, P.n_cams, gtile, &cam_idx);
+        const int64_t ltile = gtile - cam.tile_off;
+        const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
+        int lx, ly;
+        tile_pixel(tid, &lx, &ly);
+        const int u = tx * TILE + lx, v = ty * TILE + ly;
+        // the warp's 8x4 pixel block, for the per-warp bounding-box skip
+        const float bx0 = (float)(tx * TILE + (warp & 1) * 8);
+        const float by0 = (float)(ty * TILE + (warp >> 1) * 4);
+        const bool inside = u < cam.width && v < cam.height;
+        const float uf = (float)u, vf = (float)v;
+        const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
+
+        const uint2 range = P.ranges[gtile];
+        const int n_items = (int)(range.y - range.x);
+        const int n_batches = (n_items + B - 1) / B;
+        if (warp == 0 && n_batches > 0)
+            issue_batch<NS, B>(P, S, 0, range.x, min(B, n_items), cam_idx);
+        // rows staged with plain stores (unaligned semantic rows) must be
+        // visible before the first batch is read; later batches are ordered by
+        // the end-of-batch barrier
+        __syncthreads();
+
+        float T = 1.f;
+        float crgb[3] = {0.f, 0.f, 0.f}, cdep = 0.f, cn[3] = {0.f, 0.f, 0.f}, ck = 0.f;
+        float co[NS];
+#pragma unroll
+        for (int c = 0; c < NS; ++c) co[c] = 0.f;
+        uint32_t last = 0;
+        bool done = !inside;
+
+        for (int b = 0; b < n_batches; ++b) {
+            const int buf = b & 1;
+            if (warp == 0 && b + 1 < n_batches)
+                issue_batch<NS, B>(P, S, buf ^ 1, range.x + (b + 1) * B,
+                                   min(B, n_items - (b + 1) * B), cam_idx);
+            if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, WAIT_LIMIT)) timed_out = true;
+            ++loads[buf];
+            const int count = min(B, n_items - b * B);
+            const bool skip = __all_sync(0xffffffffu, done || timed_out);
+            if (!skip) {
+                for (int j = 0; j < count; ++j) {
+                    const float* rc = &S.rec[buf][j][0];
+                    if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
+                    if (done) continue;
+                    float dx, dy, Gs;
+                    const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                    ++n_eval;
+                    if (alpha < P.alpha_min) continue;
+                    const float test_T = T * (1.f - alpha);
+                    if (test_T < P.T_min) {
+                        done = true;
+                        continue;
+                    }
+                    ++n_blend;
+                    const float w = alpha * T;
+                    PairGeom G;
+                    pair_geometry(rc, xt, yt, G);
+                    const float depth = P.center_depth ? rc[R_Z] : G.t;
+                    const float nsg = (G.inside ? -G.inv_m : G.inv_m) * w;
+                    crgb[0] = fmaf(w, rc[R_RGB], crgb[0]);
+                    crgb[1] = fmaf(w, rc[R_RGB + 1], crgb[1]);
+                    crgb[2] = fmaf(w, rc[R_RGB + 2], crgb[2]);
+                    cdep = fmaf(w, depth, cdep);
+                    cn[0] = fmaf(nsg, G.m[0], cn[0]);
+                    cn[1] = fmaf(nsg, G.m[1], cn[1]);
+                    cn[2] = fmaf(nsg, G.m[2], cn[2]);
+                    ck = fmaf(w, rc[R_K], ck);
+                    accumulate_row<NS>(&S.sem[buf][j][0], w, co);
+                    T = test_T;
+                    last = (uint32_t)(b * B + j + 1);
                 }
-                ++n_blend;
-                const float w = alpha * T;
-                PairGeom G;
-                pair_geometry(rc, xt, yt, G);
-                const float depth = P.center_depth ? rc[R_Z] : G.t;
-                const float nsg = (G.inside ? -G.inv_m : G.inv_m) * w;
-                crgb[0] = fmaf(w, rc[R_RGB], crgb[0]);
-                crgb[1] = fmaf(w, rc[R_RGB + 1], crgb[1]);
-                crgb[2] = fmaf(w, rc[R_RGB + 2], crgb[2]);
-                cdep = fmaf(w, depth, cdep);
-                cn[0] = fmaf(nsg, G.m[0], cn[0]);
-                cn[1] = fmaf(nsg, G.m[1], cn[1]);
-                cn[2] = fmaf(nsg, G.m[2], cn[2]);
-                ck = fmaf(w, rc[R_K], ck);
-                accumulate_row<NS>(&S.sem[buf][j][0], w, co);
-                T = test_T;
-                last = (uint32_t)(b * BATCH + j + 1);
+            }
+            const int alive = __syncthreads_count(!done && !timed_out);
+            if (alive == 0) {
+                // drain the batch already in flight before leaving the tile
+                if (b + 1 < n_batches) {
+                    if (!mbar_wait_bounded(&S.bar[buf ^ 1], loads[buf ^ 1] & 1u, WAIT_LIMIT))
+                        timed_out = true;
+                    ++loads[buf ^ 1];
+                }
+                break;
             }
         }
-        const int alive = __syncthreads_count(!done && !timed_out);
-        if (alive == 0) {
-            // drain the batch already in flight before leaving
-            if (b + 1 < n_batches)
-                mbar_wait_bounded(&S.bar[buf ^ 1], (uint32_t)((b + 1) >> 1) & 1u, WAIT_LIMIT);
-            break;
+        if (inside) {
+            const int W = cam.width;
+            const int64_t HW = (int64_t)cam.height * W;
+            const int64_t pix = cam.pix_off;
+            const int64_t idx = (int64_t)v * W + u;
+            P.out.rgb[pix * 3 + 0 * HW + idx] = crgb[0];
+            P.out.rgb[pix * 3 + 1 * HW + idx] = crgb[1];
+            P.out.rgb[pix * 3 + 2 * HW + idx] = crgb[2];
+            P.out.depth[pix + idx] = cdep;
+            P.out.normal_g[pix * 3 + 0 * HW + idx] = cn[0];
+            P.out.normal_g[pix * 3 + 1 * HW + idx] = cn[1];
+            P.out.normal_g[pix * 3 + 2 * HW + idx] = cn[2];
+            P.out.kmap[pix + idx] = ck;
+            P.out.T_final[pix + idx] = T;
+            P.out.n_contrib[pix + idx] = last;
+            if (P.out.logits) {
+                float* lo = P.out.logits + pix * (int64_t)P.n_sem + idx;
+#pragma unroll
+                for (int c = 0; c < NS; ++c)
+                    if (c < P.n_sem) lo[(int64_t)c * HW] = co[c];
+            }
         }
+        // the end-of-batch barrier already separated this tile's last use of
+        // the shared buffers from the next tile's first issue; a bounded wait
+        // that gave up ends the CTA (uniformly)
+        if (__syncthreads_or(timed_out)) break;
     }
     if (timed_out && (tid & 31) == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
     // work counters: one atomic per warp
@@ -210,51 +242,30 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         atomicAdd(&P.hdr->n_eval, (unsigned long long)n_eval);
         atomicAdd(&P.hdr->n_blend, (unsigned long long)n_blend);
     }
-    if (!inside) return;
-    const int H = cam.height, W = cam.width;
-    const int64_t HW = (int64_t)H * W;
-    const int64_t pix = cam.pix_off;
-    const int64_t idx = (int64_t)v * W + u;
-    P.out.rgb[pix * 3 + 0 * HW + idx] = crgb[0];
-    P.out.rgb[pix * 3 + 1 * HW + idx] = crgb[1];
-    P.out.rgb[pix * 3 + 2 * HW + idx] = crgb[2];
-    P.out.depth[pix + idx] = cdep;
-    P.out.normal_g[pix * 3 + 0 * HW + idx] = cn[0];
-    P.out.normal_g[pix * 3 + 1 * HW + idx] = cn[1];
-    P.out.normal_g[pix * 3 + 2 * HW + idx] = cn[2];
-    P.out.kmap[pix + idx] = ck;
-    P.out.T_final[pix + idx] = T;
-    P.out.n_contrib[pix + idx] = last;
-    if (P.out.logits) {
-        float* lo = P.out.logits + pix * (int64_t)P.n_sem + idx;
-#pragma unroll
-        for (int c = 0; c < NS; ++c)
-            if (c < P.n_sem) lo[(int64_t)c * HW] = co[c];
-    }
 }
 
-template <int NS, typename FT>
-static void launch_fwd_t(const FwdParams& P, int64_t n_tiles, cudaStream_t st) {
-    const size_t smem = sizeof(FwdSmem<NS, FT>);
+template <int NS, int B>
+static void launch_fwd_t(const FwdParams& P, int grid, cudaStream_t st) {
+    const size_t smem = sizeof(FwdSmem<NS, B>);
     static bool attr_set = false;  // host-side, set once per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(render_fwd_kernel<NS, FT>,
+        cudaFuncSetAttribute(render_fwd_kernel<NS, B>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    render_fwd_kernel<NS, FT><<<(unsigned)n_tiles, 256, smem, st>>>(P);
+    render_fwd_kernel<NS, B><<<grid, 256, smem, st>>>(P);
 }
 
-template <typename FT>
-static void launch_fwd_ft(const FwdParams& P, int64_t n_tiles, cudaStream_t st) {
+template <int B>
+static void launch_fwd_b(const FwdParams& P, int grid, cudaStream_t st) {
     if (P.n_sem <= 8)
-        launch_fwd_t<8, FT>(P, n_tiles, st);
+        launch_fwd_t<8, B>(P, grid, st);
     else if (P.n_sem <= 16)
-        launch_fwd_t<16, FT>(P, n_tiles, st);
+        launch_fwd_t<16, B>(P, grid, st);
     else if (P.n_sem <= 32)
-        launch_fwd_t<32, FT>(P, n_tiles, st);
+        launch_fwd_t<32, B>(P, grid, st);
     else
-        launch_fwd_t<64, FT>(P, n_tiles, st);
+        launch_fwd_t<64, B>(P, grid, st);
 }
 
 int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
@@ -265,21 +276,32 @@ int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
     P.n_cams = p.n_cams;
     P.n_sem = p.n_sem;
     P.n = p.n;
+    P.n_tiles = p.n_tiles;
     P.rec = ws_ptr<float>(ws, p, OFF_REC);
-    P.sem = g.sem;
+    // bfloat16 logits are read from their float32 copy (made by the preprocess)
+    P.sem = p.feat_dtype ? ws_ptr<float>(ws, p, OFF_SEM32) : static_cast<const float*>(g.sem);
     P.vals = sorted_buffer(p) ? ws_ptr<uint32_t>(ws, p, OFF_VALS1) : ws_ptr<uint32_t>(ws, p, OFF_VALS0);
     P.ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
-    P.hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+    P.order = ws_ptr<uint32_t>(ws, p, OFF_ORDER);
+    WsHeader* hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
+    P.work = &hdr->work_fwd;
+    P.hdr = hdr;
     P.out = out;
     P.alpha_min = p.cfg.alpha_min;
     P.alpha_max = p.cfg.alpha_max;
     P.T_min = p.cfg.T_min;
     P.center_depth = (p.cfg.flags & UNIGS_FLAG_CENTER_DEPTH) ? 1 : 0;
-    // bfloat16 logits are read from their float32 copy (made by the preprocess)
-    if (p.feat_dtype) P.sem = ws_ptr<float>(ws, p, OFF_SEM32);
     P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * 4) % 16 == 0) &&
                  ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
-    launch_fwd_ft<float>(P, p.n_tiles, st);
+    cudaMemsetAsync(P.work, 0, sizeof(uint32_t), st);
+    const int ctas = p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 2;
+    int64_t grid = (int64_t)sm_count() * ctas;
+    if (grid > p.n_tiles) grid = p.n_tiles;
+    switch (p.cfg.batch) {
+        case 16: launch_fwd_b<16>(P, (int)grid, st); break;
+        case 64: launch_fwd_b<64>(P, (int)grid, st); break;
+        default: launch_fwd_b<32>(P, (int)grid, st); break;
+    }
     return 1;
 }
 

@@ -93,7 +93,9 @@ struct WsHeader {
     unsigned long long need;  // instances required (capacity errors)
     unsigned long long n_eval;   // (pixel, Gaussian) pairs whose alpha the forward evaluated
     unsigned long long n_blend;  // pairs the forward blended (alpha >= alpha_min, not stopped)
-    uint32_t pad[56];
+    uint32_t work_fwd;           // tile counters of the persistent composite kernels
+    uint32_t work_bwd;
+    uint32_t pad[54];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 
@@ -101,7 +103,7 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 enum {
     OFF_HDR = 0, OFF_CAM, OFF_REC, OFF_RECT, OFF_TOUCH, OFF_OFFS, OFF_ZBITS,
     OFF_SCAN, OFF_KEYS0, OFF_KEYS1, OFF_VALS0, OFF_VALS1, OFF_HIST, OFF_RANGES,
-    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_END
+    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_ORDER, OFF_END
 };
 
 // Per-(camera, Gaussian) record of the opacity-aware tile test (8 floats):

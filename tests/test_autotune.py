@@ -1,0 +1,70 @@
+"""Host logic of the launch-shape autotuner (no GPU): cache keys, the search
+and the JSON cache; and, on a GPU, one real search on a small scene."""
+import json
+
+import pytest
+
+from paper_2510_12174_gb300 import autotune
+
+
+def test_key_classes():
+    k = autotune.key_for("GB300", 152, 64, "bf16", [(1280, 720)] * 16, 1_000_000)
+    assert k == "GB300|sm152|sem64|bf16|cams16|px2^24|n2^20"
+    # logit counts share the kernel's compiled width
+    assert autotune.key_for("G", 1, 5, "f32", [(8, 8)], 10).split("|")[2] == "sem8"
+    assert autotune.key_for("G", 1, 17, "f32", [(8, 8)], 10).split("|")[2] == "sem32"
+    assert autotune.key_for("G", 1, 0, "f32", [(8, 8)], 10).split("|")[2] == "sem0"
+    assert autotune.key_for("G", 1, 100, "f32", [(8, 8)], 10).split("|")[2] == "sem64"
+
+
+def test_search_picks_fastest_and_caches(tmp_path):
+    path = str(tmp_path / "shapes.json")
+    cost = {(32, 2): 5.0, (16, 2): 4.0, (64, 1): 6.0}
+    calls = []
+
+    def timer(b, c):
+        calls.append((b, c))
+        return cost[(b, c)]
+
+    assert autotune.search("k", cost, path, False, timer) == (16, 2)
+    assert len(calls) == 3
+    d = json.load(open(path))
+    assert d["k"]["batch"] == 16 and d["k"]["ms"]["64x1"] == 6.0
+    # a cached key is not timed again unless forced
+    assert autotune.search("k", cost, path, False, timer) == (16, 2)
+    assert len(calls) == 3
+    cost[(64, 1)] = 1.0
+    assert autotune.search("k", cost, path, True, timer) == (64, 1)
+    # other keys are kept
+    autotune.search("other", {(32, 1): 1.0}, path, False, lambda b, c: 1.0)
+    assert set(json.load(open(path))) == {"k", "other"}
+
+
+def test_search_rejects_invalid_shapes(tmp_path):
+    with pytest.raises(ValueError):
+        autotune.search("k", [(48, 2)], str(tmp_path / "s.json"), False, lambda b, c: 1.0)
+    with pytest.raises(ValueError):
+        autotune.search("k", [(32, 0)], str(tmp_path / "s.json"), False, lambda b, c: 1.0)
+
+
+def test_corrupt_cache_is_ignored(tmp_path):
+    path = tmp_path / "s.json"
+    path.write_text("{not json")
+    assert autotune.search("k", [(32, 2)], str(path), False, lambda b, c: 1.0) == (32, 2)
+
+
+@pytest.mark.gpu
+def test_tune_on_small_scene(tmp_path):
+    import torch
+    import __graft_entry__ as ge
+    from paper_2510_12174_gb300 import rasterizer as rz
+    from paper_2510_12174_gb300 import scenes
+    ge.build()
+    sc, cams = scenes.small_room(n=4000, width=64, height=48, n_sem=16, seed=3, n_cams=2)
+    ds = rz.DeviceScene.from_scene(sc)
+    path = str(tmp_path / "s.json")
+    b, c = autotune.tune(ds, cams, candidates=[(32, 2), (16, 1)], reps=2, cache_path=path)
+    assert (b, c) in [(32, 2), (16, 1)]
+    cfg = autotune.config_for(ds, cams, cache_path=path)
+    assert (cfg.batch, cfg.ctas_per_sm) == (b, c)
+    torch.cuda.synchronize()
