@@ -45,8 +45,8 @@ def loss_terms(out: Dict[str, List[np.ndarray]], tgt: Dict[str, List[np.ndarray]
 
     out: per-camera lists 'rgb' [3,H,W], 'depth' [H,W], 'normal_d' [3,H,W],
     'kmap' [H,W], 'logits' [C,H,W].  tgt: 'rgb' [3,H,W], 'depth' [H,W] (<= 0:
-    no measurement, excluded), 'normal' [3,H,W], 'label' [H,W] int (< 0:
-    unlabelled, excluded).  Returns {term: (value, {map: gradient list})}.
+    no measurement, excluded), 'normal' [3,H,W], 'label' [H,W] int (outside
+    [0, C): unlabelled, excluded).  Returns {term: (value, {map: gradient list})}.
     """
     shapes = [np.asarray(d).shape for d in out["depth"]]
     P = sum(int(np.prod(s)) for s in shapes)
@@ -85,7 +85,7 @@ def loss_terms(out: Dict[str, List[np.ndarray]], tgt: Dict[str, List[np.ndarray]
     O = _cat(out["logits"], np.asarray(out["logits"][0]).shape[0])
     C = O.shape[0]
     lab = np.concatenate([np.asarray(l).reshape(-1) for l in tgt["label"]]).astype(np.int64)
-    has = lab >= 0
+    has = (lab >= 0) & (lab < C)
     nl = int(has.sum())
     gO = np.zeros_like(O)
     if nl:

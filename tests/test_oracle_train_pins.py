@@ -162,3 +162,15 @@ def test_prune_rule_hand_case():
     k = np.array([1.0, 1.1, 1.3, 0.85, 0.7, 0.9, 1.25, 0.79], dtype=np.float32)
     keep = ot.prune_mask(k, 0.2)
     assert keep.tolist() == [True, True, False, True, False, True, False, False]
+
+
+def test_out_of_range_labels_are_unlabelled():
+    rng = np.random.default_rng(7)
+    out, tgt = _maps(rng, [(4, 4)], C=3)
+    ref = ot.loss_terms(out, tgt)["seg"][0]
+    tgt2 = {k: [a.copy() for a in v] for k, v in tgt.items()}
+    lab = tgt2["label"][0]
+    lab[lab == -1] = 3                    # the same pixels, marked by an out-of-range id
+    r = ot.loss_terms(out, tgt2)["seg"]
+    assert r[0] == pytest.approx(ref, rel=1e-15)
+    assert np.all(r[1]["logits"][0][:, lab == 3] == 0)
