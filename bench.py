@@ -155,7 +155,8 @@ def run_ours(args):
     r = rz.Renderer(ds, cams, cfg=cfg)
     out = r.forward()                      # sizes the capacity (one read-back)
     torch.cuda.synchronize()
-    cap = int(r.last_instances * 1.15) + 65536
+    n_inst = int(r.last_instances)
+    cap = int(n_inst * 1.15) + 65536
     r = rz.Renderer(ds, cams, cfg=cfg, capacity=cap)
     out = r.alloc_outputs()
     grads = r.alloc_grads()
@@ -312,7 +313,7 @@ def run_ours(args):
         "stage_ms": {"preprocess+bin_sort": stage_ms[0], "render_fwd+normal_d": stage_ms[1],
                      "depth_normal_bwd": stage_ms[2], "render_bwd": stage_ms[3]},
         "work": {"pairs_evaluated": n_eval, "pairs_blended": n_blend,
-                 "instances": int(r.last_instances or 0),
+                 "instances": n_inst,
                  "gaussian_pixel_evals_per_s": n_eval / (ms_all / 1000.0)},
         "roofline": {"bound": "alu", "kernel": "render_bwd (composite backward + preprocess backward)",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

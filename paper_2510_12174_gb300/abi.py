@@ -1,4 +1,4 @@
-"""ctypes binding of the libunigs C ABI (include/unigs.h).
+"""ctypes binding of the libunigs C ABI (include/unigs.h, include/unigs_train.h).
 
 Argument marshalling only: every function here forwards to the entry point
 of the same name; all arithmetic runs in the library's kernels.  Loading
@@ -75,6 +75,46 @@ class unigs_plan(Structure):
                 ("off", c_size_t * 20), ("cfg", unigs_config)]
 
 
+class unigs_targets(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("normal", c_void_p),
+                ("label", c_void_p)]
+
+
+class unigs_loss_lambda(Structure):
+    _fields_ = [("l1", c_float), ("normal", c_float), ("depth", c_float), ("seg", c_float),
+                ("K", c_float)]
+
+
+class unigs_loss_grads(Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("normal_d", c_void_p),
+                ("kmap", c_void_p), ("logits", c_void_p)]
+
+
+class unigs_adam_group(Structure):
+    _fields_ = [("param", c_void_p), ("grad", c_void_p), ("m", c_void_p), ("v", c_void_p),
+                ("act_out", c_void_p), ("bf16_out", c_void_p), ("count", c_int64),
+                ("lr", c_float), ("activation", c_int32)]
+
+
+class unigs_adam_hparams(Structure):
+    _fields_ = [("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
+
+
+class unigs_prune_array(Structure):
+    _fields_ = [("src", c_void_p), ("dst", c_void_p), ("planes", c_int32), ("row", c_int32),
+                ("elem_bytes", c_int32), ("fill", c_int32), ("fill_value", c_float),
+                ("reserved", c_int32)]
+
+
+UNIGS_LOSS_TOTAL, UNIGS_LOSS_L1, UNIGS_LOSS_NORMAL, UNIGS_LOSS_DEPTH = 0, 1, 2, 3
+UNIGS_LOSS_SEG, UNIGS_LOSS_K = 4, 5
+UNIGS_LOSS_W_L1, UNIGS_LOSS_W_NORMAL, UNIGS_LOSS_W_DEPTH = 6, 7, 8
+UNIGS_LOSS_W_SEG, UNIGS_LOSS_W_K = 9, 10
+UNIGS_LOSS_N_DEPTH, UNIGS_LOSS_N_LABEL = 11, 12
+UNIGS_LOSS_RECORD_FLOATS = 16
+UNIGS_ACT_NONE, UNIGS_ACT_EXP, UNIGS_ACT_SIGMOID = 0, 1, 2
+UNIGS_ADAM_MAX_GROUPS = 16
+
 _lib = None
 
 # (name, restype, argtypes)
@@ -103,11 +143,24 @@ _SIGS = [
     ("unigs_status_string", c_char_p, [c_int32]),
     ("unigs_sort_pairs_static", c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                           c_void_p, c_void_p]),
+    # include/unigs_train.h
+    ("unigs_loss_lambda_default", None, [POINTER(unigs_loss_lambda)]),
+    ("unigs_loss", c_int32, [POINTER(unigs_plan), POINTER(unigs_outputs), c_void_p,
+                             POINTER(unigs_targets), POINTER(unigs_loss_lambda), c_void_p,
+                             c_void_p, POINTER(unigs_loss_grads), c_void_p]),
+    ("unigs_adam_step", c_int32, [POINTER(unigs_adam_group), c_int32,
+                                  POINTER(unigs_adam_hparams), c_void_p, c_void_p]),
+    ("unigs_param_copies", c_int32, [POINTER(unigs_adam_group), c_int32, c_void_p]),
+    ("unigs_prune_workspace_bytes", c_size_t, [c_int64]),
+    ("unigs_prune_mark", c_int32, [c_void_p, c_int64, c_float, c_void_p, POINTER(c_int64),
+                                   c_void_p]),
+    ("unigs_prune_compact", c_int32, [POINTER(unigs_prune_array), c_int32, c_int64, c_int64,
+                                      c_void_p, c_void_p]),
 ]
 
 
 def exported_symbols():
-    """Names of the entry points declared in include/unigs.h."""
+    """Names of the entry points declared in include/*.h."""
     return [s[0] for s in _SIGS]
 
 

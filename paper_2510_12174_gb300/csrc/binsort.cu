@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-static int scan_u32(const uint32_t* in, int64_t n, uint32_t* partial, uint32_t* out,
-                    uint32_t* total, cudaStream_t st) {
+int scan_u32(const uint32_t* in, int64_t n, uint32_t* partial, uint32_t* out, uint32_t* total,
+             cudaStream_t st) {
     const int64_t nb = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
     if (nb == 0) return 0;
     scan_reduce_kernel<<<(unsigned)nb, 256, 0, st>>>(in, n, partial);

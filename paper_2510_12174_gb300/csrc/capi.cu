@@ -162,6 +162,7 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     // float32 copy of bfloat16 semantic rows, refreshed by every preprocess
     sizes[OFF_SEM32] = g->feat_dtype ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
     sizes[OFF_ORDER] = sizeof(uint32_t) * (size_t)tiles;
+    sizes[OFF_LOSS] = sizeof(float) * 8 * (size_t)LOSS_MAX_BLOCKS;
     size_t off = 0;
     for (int r = 0; r < OFF_END; ++r) {
         plan->off[r] = off;
@@ -281,6 +282,90 @@ int32_t unigs_launches_per_step(const unigs_plan* plan) {
         conv = (cnt / 2 > 0 ? 1 : 0) + (int)(cnt & 1);
     }
     return 2 /*preprocess*/ + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ + 2 /*bwd*/;
+}
+
+// ------------------------------------------------------------ training step
+void unigs_loss_lambda_default(unigs_loss_lambda* lam) {
+    if (!lam) return;
+    lam->l1 = 1.f;
+    lam->normal = lam->depth = lam->seg = lam->K = 0.1f;
+}
+
+unigs_status unigs_loss(const unigs_plan* plan, const unigs_outputs* out, const float* normal_d,
+                        const unigs_targets* tgt, const unigs_loss_lambda* lambda, void* ws,
+                        float* record, const unigs_loss_grads* grads, unigs_stream stream) {
+    if (!plan || !out || !tgt || !lambda || !ws || !record || !grads) return UNIGS_ERR_INVALID_ARG;
+    if ((tgt->rgb && !out->rgb) || (tgt->depth && !out->depth) || (tgt->normal && !normal_d) ||
+        (tgt->label && (!out->logits || plan->n_sem == 0)))
+        return UNIGS_ERR_INVALID_ARG;
+    launch_loss(*plan, *out, normal_d, *tgt, *lambda, ws, record, *grads, (cudaStream_t)stream);
+    return cuda_status();
+}
+
+unigs_status unigs_adam_step(const unigs_adam_group* groups, int32_t n_groups,
+                             const unigs_adam_hparams* hp, int32_t* step, unigs_stream stream) {
+    if (!hp || !step || n_groups < 0 || n_groups > UNIGS_ADAM_MAX_GROUPS ||
+        (n_groups > 0 && !groups))
+        return UNIGS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_groups; ++i) {
+        const unigs_adam_group& G = groups[i];
+        if (G.count < 0 || G.activation < UNIGS_ACT_NONE || G.activation > UNIGS_ACT_SIGMOID)
+            return UNIGS_ERR_INVALID_ARG;
+        if (G.count > 0 && (!G.param || !G.grad || !G.m || !G.v)) return UNIGS_ERR_INVALID_ARG;
+        if (G.act_out == G.param && G.activation != UNIGS_ACT_NONE) return UNIGS_ERR_INVALID_ARG;
+    }
+    launch_adam(groups, n_groups, *hp, step, (cudaStream_t)stream);
+    return cuda_status();
+}
+
+unigs_status unigs_param_copies(const unigs_adam_group* groups, int32_t n_groups,
+                                unigs_stream stream) {
+    if (n_groups < 0 || n_groups > UNIGS_ADAM_MAX_GROUPS || (n_groups > 0 && !groups))
+        return UNIGS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_groups; ++i) {
+        const unigs_adam_group& G = groups[i];
+        if (G.count < 0 || G.activation < UNIGS_ACT_NONE || G.activation > UNIGS_ACT_SIGMOID)
+            return UNIGS_ERR_INVALID_ARG;
+        if (G.count > 0 && !G.param) return UNIGS_ERR_INVALID_ARG;
+        if (G.act_out == G.param && G.activation != UNIGS_ACT_NONE) return UNIGS_ERR_INVALID_ARG;
+    }
+    launch_param_copies(groups, n_groups, (cudaStream_t)stream);
+    return cuda_status();
+}
+
+size_t unigs_prune_workspace_bytes(int64_t n) { return n < 0 ? 0 : prune_ws_bytes(n); }
+
+unigs_status unigs_prune_mark(const float* k, int64_t n, float T_k, void* prune_ws,
+                              int64_t* n_keep, unigs_stream stream) {
+    if (n < 0 || n > 0xffffffffLL || (n > 0 && !k) || !prune_ws || !aligned16(prune_ws) || !n_keep)
+        return UNIGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_prune_mark(k, n, T_k, prune_ws, st);
+    unigs_status s = cuda_status();
+    if (s != UNIGS_OK) return s;
+    uint32_t cnt = 0;
+    if (cudaMemcpyAsync(&cnt, prune_count_ptr(prune_ws, n), sizeof(cnt), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return UNIGS_ERR_CUDA;
+    *n_keep = (int64_t)cnt;
+    return UNIGS_OK;
+}
+
+unigs_status unigs_prune_compact(const unigs_prune_array* arrays, int32_t n_arrays, int64_t n,
+                                 int64_t n_keep, const void* prune_ws, unigs_stream stream) {
+    if (n < 0 || n_keep < 0 || n_keep > n || n_arrays < 0 || (n_arrays > 0 && !arrays) ||
+        !prune_ws)
+        return UNIGS_ERR_INVALID_ARG;
+    for (int a = 0; a < n_arrays; ++a) {
+        const unigs_prune_array& A = arrays[a];
+        if (A.planes < 1 || A.row < 1 || (A.elem_bytes != 4 && A.elem_bytes != 2) ||
+            (A.fill && A.elem_bytes != 4) || (!A.fill && n > 0 && !A.src) ||
+            (n_keep > 0 && !A.dst) || (A.src && A.src == A.dst))
+            return UNIGS_ERR_INVALID_ARG;
+    }
+    launch_prune_compact(arrays, n_arrays, n, n_keep, prune_ws, (cudaStream_t)stream);
+    return cuda_status();
 }
 
 const char* unigs_status_string(unigs_status s) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "unigs_internal.cuh"
+#include "unigs_train.h"
 
 namespace unigs {
 
@@ -27,6 +28,24 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
 int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long long* kout,
                uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
                int shift, int nb, cudaStream_t st);
+
+// Exclusive scan of n uint32 (three launches); partial holds
+// ceil(n / SCAN_ITEMS) counters; *total (optional, device) gets the sum.
+int scan_u32(const uint32_t* in, int64_t n, uint32_t* partial, uint32_t* out, uint32_t* total,
+             cudaStream_t st);
+
+// Training step (losses, Adam, pruning).
+int launch_loss(const unigs_plan& p, const unigs_outputs& out, const float* normal_d,
+                const unigs_targets& tgt, const unigs_loss_lambda& lam, void* ws, float* record,
+                const unigs_loss_grads& g, cudaStream_t st);
+int launch_adam(const unigs_adam_group* groups, int n_groups, const unigs_adam_hparams& hp,
+                int32_t* step, cudaStream_t st);
+int launch_param_copies(const unigs_adam_group* groups, int n_groups, cudaStream_t st);
+size_t prune_ws_bytes(int64_t n);
+int launch_prune_mark(const float* k, int64_t n, float T_k, void* ws, cudaStream_t st);
+uint32_t* prune_count_ptr(void* ws, int64_t n);
+int launch_prune_compact(const unigs_prune_array* arrays, int n_arrays, int64_t n, int64_t n_keep,
+                         const void* ws, cudaStream_t st);
 
 // Number of SMs of the current device (queried once per device).
 int sm_count();

@@ -103,7 +103,7 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 enum {
     OFF_HDR = 0, OFF_CAM, OFF_REC, OFF_RECT, OFF_TOUCH, OFF_OFFS, OFF_ZBITS,
     OFF_SCAN, OFF_KEYS0, OFF_KEYS1, OFF_VALS0, OFF_VALS1, OFF_HIST, OFF_RANGES,
-    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_ORDER, OFF_END
+    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_ORDER, OFF_LOSS, OFF_END
 };
 
 // Per-(camera, Gaussian) record of the opacity-aware tile test (8 floats):
@@ -158,6 +158,7 @@ __device__ __forceinline__ bool tile_keep(const float* __restrict__ cr, int tx, 
 
 constexpr int SORT_ITEMS = 2048;   // keys per sort block (256 threads x 8)
 constexpr int SCAN_ITEMS = 4096;   // elements per scan block (256 threads x 16)
+constexpr int LOSS_MAX_BLOCKS = 2048;  // block partials of the loss reduction
 
 template <typename T>
 __host__ __device__ inline T* ws_ptr(void* ws, const unigs_plan& p, int region) {

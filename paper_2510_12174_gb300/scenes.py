@@ -328,3 +328,61 @@ def small_room(n: int = 8000, width: int = 100, height: int = 76, n_sem: int = 8
         cams = orbit_cameras(n_cams, seed=seed + 100,
                              resolutions=[(width, height), (width + 28, height - 20)])
     return sc, cams
+
+
+def config5(n: int = 6_000_000):
+    """Training workload: 6M room Gaussians, 8 orbit cameras at 1920x1080,
+    64 logits, BF16 features."""
+    sc = make_scene("room", n, 64, 3, seed=4, log_scale_mean=-4.5,
+                    log_scale_std=1.0, log_scale_max=-1.0, feat_bf16=True)
+    return sc, orbit_cameras(8, seed=15, resolutions=[(1920, 1080)])
+
+
+def perturb(scene: "Scene", seed: int, sigma_mean: float = 0.01,
+            sigma_log_scale: float = 0.1) -> "Scene":
+    """A copy of ``scene`` with jittered centres and scales (the scene whose
+    renders serve as training targets)."""
+    rng = np.random.default_rng(seed)
+    f32 = np.float32
+    mean = (scene.mean + rng.normal(0, sigma_mean, scene.mean.shape)).astype(f32)
+    scale = (scene.scale * np.exp(rng.normal(0, sigma_log_scale, scene.scale.shape))).astype(f32)
+    return dataclasses.replace(scene, mean=mean, scale=scale)
+
+
+def synthetic_maps(cams: Sequence[Camera], n_sem: int, seed: int) -> dict:
+    """Stand-ins for rendered maps, per camera: rgb U(0,1), depth U(1,4),
+    unit normal_d (10% of pixels zero, as where the stencil leaves the image),
+    kmap U(0.5,1.5), logits N(0, 4)."""
+    rng = np.random.default_rng(seed)
+    out = {k: [] for k in ("rgb", "depth", "normal_d", "kmap", "logits")}
+    for c in cams:
+        H, W = c.height, c.width
+        out["rgb"].append(rng.uniform(0, 1, (3, H, W)).astype(np.float32))
+        out["depth"].append(rng.uniform(1, 4, (H, W)).astype(np.float32))
+        n = rng.normal(size=(3, H, W))
+        n /= np.linalg.norm(n, axis=0)
+        n[:, rng.uniform(size=(H, W)) < 0.1] = 0.0
+        out["normal_d"].append(n.astype(np.float32))
+        out["kmap"].append(rng.uniform(0.5, 1.5, (H, W)).astype(np.float32))
+        out["logits"].append(rng.normal(0, 2, (n_sem, H, W)).astype(np.float32))
+    return out
+
+
+def synthetic_targets(cams: Sequence[Camera], n_sem: int, seed: int) -> dict:
+    """Training targets, per camera: rgb U(0,1); depth U(1,4) with 15% of the
+    pixels unmeasured (0); unit normals; labels uniform in [0, n_sem) with
+    10% unlabelled (-1)."""
+    rng = np.random.default_rng(seed)
+    out = {k: [] for k in ("rgb", "depth", "normal", "label")}
+    for c in cams:
+        H, W = c.height, c.width
+        out["rgb"].append(rng.uniform(0, 1, (3, H, W)).astype(np.float32))
+        d = rng.uniform(1, 4, (H, W))
+        d[rng.uniform(size=(H, W)) < 0.15] = 0.0
+        out["depth"].append(d.astype(np.float32))
+        n = rng.normal(size=(3, H, W))
+        out["normal"].append((n / np.linalg.norm(n, axis=0)).astype(np.float32))
+        lab = rng.integers(0, max(n_sem, 1), (H, W))
+        lab[rng.uniform(size=(H, W)) < 0.1] = -1
+        out["label"].append(lab.astype(np.int32))
+    return out
