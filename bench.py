@@ -15,6 +15,12 @@ Inputs (parameters, workspace, outputs) are far larger than the 129 MB L2, so
 no flush is needed between steps.  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload.
 
+``e2e`` runs the same 16 views through the public API with the combined loss
+of Sec. 3.4 driving the backward, the targets copied from pinned host memory
+every step and the loss record read back.  ``train_step`` times one training
+iteration (forward, loss, backward, Adam) of the 6M-Gaussian, 8 x 1080p
+workload and the HBM-bound Adam and loss kernels against the HBM peak.
+
 Multi-GPU: the path renders independent views, so N ranks are N replicas
 (weak scaling, no collective); ``value`` sums the views of all ranks.
 """
@@ -144,8 +150,7 @@ def run_ours(args):
     n_sem = sc.n_sem
     up = scenes.upstream_grads(cams, n_sem, seed=5)
     keys = ("rgb", "depth", "normal_g", "kmap", "logits", "normal_d")
-    host_up = {k: torch.from_numpy(np.concatenate([a.ravel() for a in up[k]])).pin_memory()
-               for k in keys}
+    host_up = {k: torch.from_numpy(np.concatenate([a.ravel() for a in up[k]])) for k in keys}
     dev_up = {k: v.to(dev) for k, v in host_up.items()}
 
     # ------------------------------------------------ batched (BF16, graph)
@@ -238,21 +243,50 @@ def run_ours(args):
     stage_ms = acc / reps
 
     # ------------------------------------------------ e2e through host buffers
+    # The same 16 views through the public API, with the combined loss of
+    # Sec. 3.4 driving the backward: every step copies that step's targets
+    # from pinned host memory, renders, evaluates the loss, back-propagates
+    # and reads the loss record back.
+    tg = scenes.synthetic_targets(cams, n_sem, seed=6)
+    host_tg = {k: torch.from_numpy(np.concatenate([a.ravel() for a in tg[k]])).pin_memory()
+               for k in tg}
+    dev_tg = {k: v.to(dev) for k, v in host_tg.items()}
+    record = torch.zeros(16, device=dev)
+    lg = r.alloc_loss_grads()
+
+    def e2e_step():
+        r.forward(out, readback=False)
+        r.loss(out, dev_tg, record, lg)
+        r.backward(out, lg, grads=grads, g_depth_buf=gbuf)
+
+    s_side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_side):
+        for _ in range(2):
+            e2e_step()
+    torch.cuda.current_stream().wait_stream(s_side)
+    torch.cuda.synchronize()
+    graph_e2e = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_e2e):
+        e2e_step()
     res_host = torch.empty(16, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        graph_e2e.replay()
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 5))
     e2.record(stream)
     for _ in range(e2e_steps):
-        for k in keys:
-            dev_up[k].copy_(host_up[k], non_blocking=True)
-        graph.replay()
-        res_host.copy_(grads["mean"].view(-1)[:16], non_blocking=True)
+        for k in dev_tg:
+            dev_tg[k].copy_(host_tg[k], non_blocking=True)
+        graph_e2e.replay()
+        res_host.copy_(record, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2.elapsed_time(e3) / e2e_steps
-    h2d = sum(v.numel() * v.element_size() for v in host_up.values())
+    h2d = sum(v.numel() * v.element_size() for v in host_tg.values())
+    e2e_loss = float(res_host[0])
+    del graph_e2e, dev_tg, host_tg, lg
 
     # ------------------------------------------------ per-view FP32 path
     pv = None
@@ -320,10 +354,18 @@ def run_ours(args):
                      "frac": achieved / fp32_peak, "traffic": None,
                      "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"},
         "e2e": {"value": N_VIEWS / (e2e_ms / 1000.0) * world, "unit": "views/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 64},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 64,
+                "note": "per step: targets (rgb, depth, normal, label) host->device from pinned "
+                        "memory, forward, combined loss (Sec. 3.4), backward, loss record "
+                        "device->host", "loss": e2e_loss},
         "gpu_launches": r.launches_per_step() * args.steps,
         "clocks": clocks,
     }
+    if not args.skip_train:
+        del graph, r, out, grads, gbuf, dev_up
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["train_step"] = train_bench(args, dev, peaks)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_tiles, peaks_note=src)
     if rank == 0:
@@ -331,6 +373,108 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def train_bench(args, dev, peaks):
+    """One training iteration of the 6M-Gaussian workload (8 orbit views at
+    1920x1080, 64 logits, BF16 feature copies): forward, combined loss,
+    backward, Adam over every parameter array - one CUDA graph per step.
+    Also times the two HBM-bound training kernels alone against the HBM peak:
+    Adam (bytes: every raw value, gradient and moment read; raw value and
+    moments written; activated float32 or bfloat16 copy written) and the loss
+    (both passes read every output and target channel; the gradient pass
+    writes the gradient maps)."""
+    import numpy as np
+    import torch
+
+    from paper_2510_12174_gb300 import rasterizer as rz
+    from paper_2510_12174_gb300 import scenes
+    from paper_2510_12174_gb300 import train as tr
+
+    sc, cams = scenes.config5(n=args.train_gauss)
+    tsc = scenes.perturb(sc, seed=5)
+    # targets: renders of the perturbed scene (rgb, depth, normal-from-depth)
+    # and uniform labels with 10% unlabelled
+    rt = rz.Renderer(rz.DeviceScene.from_scene(tsc, device=dev, feat_bf16=True), cams)
+    o = rt.forward()
+    lab = scenes.synthetic_targets(cams, sc.n_sem, seed=7)["label"]
+    targets = {"rgb": o["rgb"].clone(), "depth": o["depth"].clone(),
+               "normal": o["normal_d"].clone(),
+               "label": torch.as_tensor(np.concatenate([a.ravel() for a in lab]), device=dev)}
+    del rt, o
+    torch.cuda.synchronize()
+    T = tr.Trainer.from_scene(sc, cams, targets, tr.TrainConfig(prune_every=0), device=dev)
+    del sc, tsc
+    T.step()                              # sizes the instance capacity (one read-back)
+    torch.cuda.synchronize()
+
+    def body():
+        T.forward(readback=False)
+        T.loss()
+        T.backward()
+        T.adam()
+
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        body()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        body()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(2, min(args.steps, 5))
+    e0.record(st)
+    for _ in range(steps):
+        g.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s, _ = T.renderer.status()
+    losses = T.losses()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    adam_ms = timed(T.adam)
+    loss_ms = timed(T.loss)
+    adam_bytes = 0
+    for name in tr.PARAMS:
+        cnt = T.raw[name].numel()
+        extra = 4 if name in ("log_scale", "logit_opacity") else (2 if name in ("sh", "sem") else 0)
+        adam_bytes += cnt * (16 + 12 + extra)
+    P = T.renderer.n_pixels
+    C = T.scene.n_sem
+    loss_bytes = P * (2 * 4 * (8 + C) + 2 * 4 * 8 + 4 * (8 + C))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    views = len(cams)
+    res = {"workload": f"{args.train_gauss // 1_000_000}M-Gaussian synthetic room, 8 orbit views "
+                       "at 1920x1080, 64 logits, BF16 feature copies, FP32 masters",
+           "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "views_per_s": views * 1000.0 / ms,
+           "status": int(s), "loss": losses,
+           "adam": {"ms": adam_ms, "bytes": adam_bytes, "achieved_gbs": adam_bytes / adam_ms / 1e6,
+                    "frac_of_hbm": adam_bytes / adam_ms / 1e6 / hbm},
+           "loss_kernels": {"ms": loss_ms, "bytes": loss_bytes,
+                            "achieved_gbs": loss_bytes / loss_ms / 1e6,
+                            "frac_of_hbm": loss_bytes / loss_ms / 1e6 / hbm},
+           "steps": steps, "path": "one CUDA graph per step (prune every 3000 steps, outside)"}
+    del g, T
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
 
 
 _CPU_SCENE = None
@@ -408,9 +552,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
-    ap.add_argument("--cpu-tiles", type=int, default=12)
+    ap.add_argument("--cpu-tiles", type=int, default=120)
     ap.add_argument("--skip-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-train", action="store_true",
+                    help="leave out the training-step measurement")
+    ap.add_argument("--train-gauss", type=int, default=6_000_000)
     ap.add_argument("--batch", type=int, default=0, choices=[0, 16, 32, 64],
                     help="Gaussians staged per batch by the composites (0: library default)")
     ap.add_argument("--ctas", type=int, default=0,

@@ -230,6 +230,36 @@ class Renderer:
                                        self._out_struct(out), go, pg, st), "unigs_render_bwd")
         return grads
 
+    # ------------------------------------------------------------------ loss
+    def alloc_loss_grads(self) -> Dict[str, torch.Tensor]:
+        P = self.n_pixels
+        f = lambda c: torch.empty(c * P, dtype=torch.float32, device=self.device)
+        return {"rgb": f(3), "depth": f(1), "normal_d": f(3), "kmap": f(1),
+                "logits": f(self.scene.n_sem)}
+
+    def loss(self, out: Dict[str, torch.Tensor], targets: Dict[str, Optional[torch.Tensor]],
+             record: torch.Tensor, lgrads: Dict[str, torch.Tensor], lam=None) -> torch.Tensor:
+        """The combined loss of Sec. 3.4 (unigs_loss, include/unigs_train.h)
+        on the outputs of the last forward: fills ``record`` (device float[16])
+        and the gradients ``lgrads`` (rgb, depth, normal_d, kmap, logits),
+        which :meth:`backward` takes as its upstream gradients."""
+        t = abi.unigs_targets()
+        t.rgb, t.depth = _ptr(targets.get("rgb")), _ptr(targets.get("depth"))
+        t.normal = _ptr(targets.get("normal"))
+        t.label = _ptr(targets.get("label")) if self.scene.n_sem else None
+        g = abi.unigs_loss_grads()
+        for k in ("rgb", "depth", "normal_d", "kmap", "logits"):
+            x = lgrads.get(k)
+            setattr(g, k, _ptr(x) if x is not None and x.numel() else None)
+        if lam is None:
+            lam = abi.unigs_loss_lambda()
+            abi.lib().unigs_loss_lambda_default(ctypes.byref(lam))
+        abi.check(abi.lib().unigs_loss(ctypes.byref(self.plan), ctypes.byref(self._out_struct(out)),
+                                       _ptr(out["normal_d"]), ctypes.byref(t), ctypes.byref(lam),
+                                       self.ws.data_ptr(), record.data_ptr(), ctypes.byref(g),
+                                       self._stream()), "unigs_loss")
+        return record
+
     # ----------------------------------------------------------------- misc
     def status(self):
         d = ctypes.c_int64(0)

@@ -120,11 +120,8 @@ class Trainer:
         self.renderer = rz.Renderer(self.scene, self.cams, cfg=self.render_cfg)
         self.out = self.renderer.alloc_outputs()
         self.grads = self.renderer.alloc_grads()
-        P = self.renderer.n_pixels
-        f = lambda c: torch.empty(c * P, dtype=torch.float32, device=dev)
-        self.lgrad = {"rgb": f(3), "depth": f(1), "normal_d": f(3), "kmap": f(1),
-                      "logits": f(self.scene.n_sem)}
-        self.g_depth_buf = f(1)
+        self.lgrad = self.renderer.alloc_loss_grads()
+        self.g_depth_buf = torch.empty(self.renderer.n_pixels, dtype=torch.float32, device=dev)
         self._sized = False
 
     def _groups(self, with_grads: bool):
@@ -166,21 +163,7 @@ class Trainer:
     def loss(self):
         """unigs_loss on the last forward; fills the loss gradients and the
         device record."""
-        r = self.renderer
-        t = abi.unigs_targets()
-        t.rgb = rz._ptr(self.targets.get("rgb"))
-        t.depth = rz._ptr(self.targets.get("depth"))
-        t.normal = rz._ptr(self.targets.get("normal"))
-        t.label = rz._ptr(self.targets.get("label")) if self.scene.n_sem else None
-        g = abi.unigs_loss_grads()
-        for k in ("rgb", "depth", "normal_d", "kmap", "logits"):
-            setattr(g, k, rz._ptr(self.lgrad[k]) if self.lgrad[k].numel() else None)
-        abi.check(abi.lib().unigs_loss(ctypes.byref(r.plan), ctypes.byref(r._out_struct(self.out)),
-                                       rz._ptr(self.out["normal_d"]), ctypes.byref(t),
-                                       ctypes.byref(self.lam), r.ws.data_ptr(),
-                                       self.record.data_ptr(), ctypes.byref(g), r._stream()),
-                  "unigs_loss")
-        return self.record
+        return self.renderer.loss(self.out, self.targets, self.record, self.lgrad, self.lam)
 
     def backward(self):
         up = {"rgb": self.lgrad["rgb"], "depth": self.lgrad["depth"],
