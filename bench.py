@@ -103,6 +103,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(ms_local: float, world: int, device) -> tuple:
+    """Whole-job time and throughput of N independent replicas: the slowest
+    rank's ms per step, and the views of every rank over that time."""
+    ms_all = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_all], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    return ms_all, world * N_VIEWS / (ms_all / 1000.0)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -202,13 +215,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_all = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * N_VIEWS / (ms_all / 1000.0)
+    ms_all, value = aggregate(ms, world, dev)
 
     # stage times (same kernels, outside the graph, CUDA events on the stream)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
