@@ -103,6 +103,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def launch_shape(cfg, simt_logits: bool) -> dict:
+    """The composites' launch shapes after the library's defaults."""
+    bwd = (int(cfg.batch) or 32, int(cfg.ctas_per_sm) or 2)
+    if simt_logits:
+        fwd = (int(cfg.batch_fwd) or bwd[0], int(cfg.ctas_per_sm_fwd) or bwd[1])
+    else:
+        fwd = (int(cfg.batch_fwd) or 16, min(int(cfg.ctas_per_sm_fwd) or 4, 4))
+    return {"fwd": {"batch": fwd[0], "ctas_per_sm": fwd[1]},
+            "bwd": {"batch": bwd[0], "ctas_per_sm": bwd[1]}}
+
+
 def aggregate(ms_local: float, world: int, device) -> tuple:
     """Whole-job time and throughput of N independent replicas: the slowest
     rank's ms per step, and the views of every rank over that time."""
@@ -170,6 +181,9 @@ def run_ours(args):
     ds = rz.DeviceScene.from_scene(sc, device=dev, feat_bf16=True)
     cfg = abi.unigs_config_default()
     cfg.batch, cfg.ctas_per_sm = args.batch, args.ctas
+    cfg.batch_fwd, cfg.ctas_per_sm_fwd = args.batch_fwd, args.ctas_fwd
+    if args.simt_logits:
+        cfg.flags |= abi.UNIGS_FLAG_SIMT_LOGITS
     r = rz.Renderer(ds, cams, cfg=cfg)
     out = r.forward()                      # sizes the capacity (one read-back)
     torch.cuda.synchronize()
@@ -348,8 +362,8 @@ def run_ours(args):
                    "resolution": "1280x720", "n_sem": n_sem, "features": "bf16 storage",
                    "path": "batched, one CUDA graph per step", "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (no flush)",
-                   "launch_shape": {"batch": int(r.cfg.batch) or 32,
-                                    "ctas_per_sm": int(r.cfg.ctas_per_sm) or 2}},
+                   "launch_shape": launch_shape(r.cfg, args.simt_logits),
+                   "logit_blend": "fp32 pipes" if args.simt_logits else "tensor cores"},
         "per_view": pv,
         "stage_ms": {"preprocess+bin_sort": stage_ms[0], "render_fwd+normal_d": stage_ms[1],
                      "depth_normal_bwd": stage_ms[2], "render_bwd": stage_ms[3]},
@@ -565,10 +579,16 @@ def main():
     ap.add_argument("--skip-train", action="store_true",
                     help="leave out the training-step measurement")
     ap.add_argument("--train-gauss", type=int, default=6_000_000)
+    ap.add_argument("--simt-logits", action="store_true",
+                    help="blend the logits on the FP32 pipes instead of the tensor cores")
     ap.add_argument("--batch", type=int, default=0, choices=[0, 16, 32, 64],
                     help="Gaussians staged per batch by the composites (0: library default)")
     ap.add_argument("--ctas", type=int, default=0,
                     help="persistent composite CTAs per SM (0: library default)")
+    ap.add_argument("--batch-fwd", type=int, default=0, choices=[0, 16, 32, 64],
+                    help="forward composite batch (0: library default)")
+    ap.add_argument("--ctas-fwd", type=int, default=0,
+                    help="forward composite CTAs per SM (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

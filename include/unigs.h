@@ -134,23 +134,33 @@ typedef struct {
 /* Compositing and normal-from-depth settings.  unigs_config_default() fills
  * alpha_min 1/255, alpha_max 0.99, T_min 1e-4, lowpass 0.3 (the 3DGS values
  * the paper keeps, Sec. 3.4), step1 1, step2 2, lambda 0.5 (Alg. 1; the
- * paper does not print its values), and the launch shape batch 32, 2 CTAs
- * per SM (the results do not depend on the launch shape beyond float32
- * atomic summation order). */
+ * paper does not print its values), and 0 (= the library's choice) for every
+ * launch-shape field.  The launch shape changes the speed only: the forward
+ * outputs do not depend on it (the tensor-core logit blend: up to float32
+ * summation order), the gradients up to float32 atomic summation order. */
 typedef struct {
     float alpha_min, alpha_max, T_min, lowpass;
     int32_t step1, step2; /* 1..4 */
     float lambda;
     uint32_t flags;       /* bit 0: UNIGS_FLAG_CENTER_DEPTH (depth of the
                              Gaussian centre instead of the midpoint, the
-                             ablation of Tab. 6) */
-    int32_t batch;        /* Gaussians staged per batch by the composite
-                             kernels: 16, 32 or 64 (0 = 32) */
-    int32_t ctas_per_sm;  /* persistent CTAs per SM of the composite kernels,
-                             1..8 (0 = 2) */
+                             ablation of Tab. 6); bit 1:
+                             UNIGS_FLAG_SIMT_LOGITS (blend the logits on the
+                             FP32 pipes even where the tensor-core blend
+                             applies) */
+    int32_t batch;        /* Gaussians staged per batch by the backward
+                             composite (and by the FP32-pipe forward when
+                             batch_fwd is 0): 16, 32 or 64 (0 = 32) */
+    int32_t ctas_per_sm;  /* persistent CTAs per SM, likewise, 1..8 (0 = 2) */
+    int32_t batch_fwd;    /* forward composite: 16, 32 or 64; 0 = 16 on the
+                             tensor-core path, else batch */
+    int32_t ctas_per_sm_fwd; /* forward composite, 1..8 (the tensor-core path
+                             caps it at 4); 0 = 4 on the tensor-core path,
+                             else ctas_per_sm */
 } unigs_config;
 
 #define UNIGS_FLAG_CENTER_DEPTH 1u
+#define UNIGS_FLAG_SIMT_LOGITS 2u
 
 /* Host-side plan: sizes and workspace offsets for one (Gaussians, cameras)
  * configuration.  Filled by unigs_plan_init; owned by the caller; read-only
@@ -205,9 +215,15 @@ unigs_status unigs_bin_sort(const unigs_plan* plan, void* ws, int64_t* n_instanc
                             unigs_stream stream);
 
 /* Forward composite, Alg. 2 (T initialised to 1; k blended, not t; colour
- * from SH): one CTA per 16x16 tile, Gaussian batches staged in shared memory
- * by bulk (TMA) copies, per-pixel accumulators in registers, early exit when
- * every pixel of the tile has T < T_min. */
+ * from SH): persistent CTAs pull 16x16 tiles longest list first, Gaussian
+ * batches staged in shared memory by bulk (TMA) copies, per-pixel
+ * accumulators in registers, early exit when every pixel of the tile has
+ * T < T_min.  With bfloat16 features and 9..64 logits (and without
+ * UNIGS_FLAG_SIMT_LOGITS) the logit blend of Eq. semantic_render runs on the
+ * tensor cores as a per-batch product W F (weights split into two bfloat16
+ * parts, float32 accumulation in tensor memory); the other channels do not
+ * change.  Non-finite logits are outside the contract (on the tensor-core
+ * path they reach every pixel of the tile batch). */
 unigs_status unigs_render_fwd(const unigs_plan* plan, const unigs_gaussians* g, void* ws,
                               const unigs_outputs* out, unigs_stream stream);
 

@@ -2,27 +2,29 @@
 
 The composites (forward Alg. 2 and backward Alg. 4) are persistent kernels
 whose CTAs pull 16x16 tiles from a device work counter, longest Gaussian list
-first.  Two launch parameters change their speed but not their results:
+first.  Two launch parameters per kernel change their speed but not their
+results:
 
-* ``batch``: Gaussians staged per shared-memory batch (16, 32 or 64).  Larger
+* the batch: Gaussians staged per shared-memory batch (16, 32 or 64).  Larger
   batches amortise the barrier and bulk-copy issue per Gaussian; smaller ones
-  waste less of the last batch of short lists.
-* ``ctas_per_sm``: resident persistent CTAs per SM (1-3).  More CTAs hide the
-  barrier and atomic latency of the backward; fewer leave more shared memory
-  per CTA (the backward's 64-logit, batch-64 stage needs ~123 KB).
+  waste less of the last batch of short lists and need less shared memory.
+* CTAs per SM (1-4): more CTAs hide barrier, MMA and atomic latency; fewer
+  leave more registers and shared memory per CTA.
 
-The forward output is bit-identical for every shape (each pixel blends its
-list in the same order); the gradients differ only in the order of float32
-atomic additions.  The tile itself stays 16x16 pixels: it is the binning unit
-whose keys and ranges the library reproduces bit for bit, so it is not a
-tuning knob.
+The forward output is bit-identical for every shape on the FP32-pipe path
+(each pixel blends its list in the same order) and moves by float32 summation
+order on the tensor-core logit blend; the gradients move by the order of
+float32 atomic additions.  The tile itself stays 16x16 pixels: it is the
+binning unit whose keys and ranges the library reproduces bit for bit, so it
+is not a tuning knob.
 
-:func:`tune` times forward + backward of each candidate on the caller's scene
-and cameras with CUDA events and keeps the fastest; results are cached in a
-JSON file keyed by :func:`workload_key` (GPU, SM count, logit class, feature
-dtype, camera count and pixel/Gaussian magnitudes), so a training run pays the
-search once per workload class.  :func:`config_for` returns a
-``unigs_config`` with the cached shape (or the library default).
+:func:`tune` times the forward candidates on the forward alone and the
+backward candidates on the backward alone (CUDA events on the caller's scene
+and cameras), keeps the fastest of each, and caches them in a JSON file keyed
+by :func:`workload_key` (GPU, SM count, logit class, feature dtype, camera
+count and pixel/Gaussian magnitudes), so a training run pays the search once
+per workload class.  :func:`config_for` returns a ``unigs_config`` with the
+cached shapes (or the library defaults).
 """
 from __future__ import annotations
 
@@ -36,8 +38,8 @@ import torch
 from . import abi
 from . import rasterizer as rz
 
-CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (32, 2), (16, 2), (64, 1), (64, 2), (32, 1), (32, 3), (16, 3))
+FWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 4), (16, 3), (32, 2), (16, 2), (64, 2))
+BWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((32, 2), (16, 2), (64, 1), (32, 3), (16, 3))
 
 
 def default_cache_path() -> str:
@@ -96,10 +98,12 @@ def _store(path: str, key: str, entry: dict) -> None:
     os.replace(tmp, path)
 
 
-def make_config(batch: int, ctas_per_sm: int, base: Optional[abi.unigs_config] = None):
+def make_config(batch: int = 0, ctas_per_sm: int = 0, base: Optional[abi.unigs_config] = None,
+                batch_fwd: int = 0, ctas_per_sm_fwd: int = 0):
     cfg = (abi.unigs_config.from_buffer_copy(base) if base is not None
            else abi.unigs_config_default())
     cfg.batch, cfg.ctas_per_sm = int(batch), int(ctas_per_sm)
+    cfg.batch_fwd, cfg.ctas_per_sm_fwd = int(batch_fwd), int(ctas_per_sm_fwd)
     return cfg
 
 
@@ -112,50 +116,65 @@ def _synthetic_upstream(r: "rz.Renderer", seed: int) -> Dict[str, torch.Tensor]:
     return up
 
 
-def time_shape(scene, cams, batch: int, ctas_per_sm: int, reps: int = 3,
-               base: Optional[abi.unigs_config] = None, seed: int = 0) -> float:
-    """Milliseconds of one forward (preprocess, sort, composite) + backward at
-    the given launch shape, median of ``reps`` after one warm-up."""
-    r = rz.Renderer(scene, cams, cfg=make_config(batch, ctas_per_sm, base))
-    out = r.forward()                       # sizes the instance capacity
-    up = _synthetic_upstream(r, seed)
-    grads = r.alloc_grads()
-    stream = torch.cuda.current_stream(r.device)
-    r.backward(out, up, grads=grads)
+def _median_ms(fn, stream, reps: int) -> float:
     times = []
     for _ in range(max(1, reps)):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r.forward(out, readback=False, normal_d=False)
-        r.backward(out, up, grads=grads)
+        fn()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-    s, need = r.status()
-    abi.check(s, f"launch shape ({batch}, {ctas_per_sm})")
     times.sort()
     return times[len(times) // 2]
 
 
-def tune(scene, cams, candidates: Iterable[Tuple[int, int]] = CANDIDATES, reps: int = 3,
-         base: Optional[abi.unigs_config] = None, cache_path: Optional[str] = None,
-         force: bool = False, timer=None) -> Tuple[int, int]:
-    """Fastest (batch, ctas_per_sm) for this scene and camera set; cached.
+def time_shape(scene, cams, batch: int, ctas_per_sm: int, reps: int = 3,
+               base: Optional[abi.unigs_config] = None, seed: int = 0,
+               stage: str = "bwd") -> float:
+    """Milliseconds of the forward composite (stage "fwd": preprocess, sort
+    and forward at the shape) or of the backward (stage "bwd"), median of
+    ``reps`` after one warm-up."""
+    cfg = (make_config(0, 0, base, batch, ctas_per_sm) if stage == "fwd"
+           else make_config(batch, ctas_per_sm, base))
+    r = rz.Renderer(scene, cams, cfg=cfg)
+    out = r.forward()                       # sizes the instance capacity
+    stream = torch.cuda.current_stream(r.device)
+    if stage == "fwd":
+        ms = _median_ms(lambda: r.forward(out, readback=False, normal_d=False), stream, reps)
+    else:
+        up = _synthetic_upstream(r, seed)
+        grads = r.alloc_grads()
+        r.backward(out, up, grads=grads)
+        ms = _median_ms(lambda: r.backward(out, up, grads=grads), stream, reps)
+    s, _ = r.status()
+    abi.check(s, f"launch shape ({batch}, {ctas_per_sm})")
+    return ms
 
-    ``timer(batch, ctas_per_sm) -> ms`` replaces the CUDA-event timing of
-    :func:`time_shape` (for callers with their own step to time)."""
+
+def tune(scene, cams, fwd_candidates: Iterable[Tuple[int, int]] = FWD_CANDIDATES,
+         bwd_candidates: Iterable[Tuple[int, int]] = BWD_CANDIDATES, reps: int = 3,
+         base: Optional[abi.unigs_config] = None, cache_path: Optional[str] = None,
+         force: bool = False, timer=None) -> Dict[str, Tuple[int, int]]:
+    """Fastest forward and backward (batch, ctas_per_sm) for this scene and
+    camera set, cached: {"fwd": (b, c), "bwd": (b, c)}.
+
+    ``timer(stage, batch, ctas_per_sm) -> ms`` replaces the CUDA-event timing
+    of :func:`time_shape`."""
     path = cache_path or default_cache_path()
     key = workload_key(scene, cams)
-    return search(key, candidates, path, force,
-                  timer or (lambda b, c: time_shape(scene, cams, b, c, reps=reps, base=base)))
+    t = timer or (lambda st, b, c: time_shape(scene, cams, b, c, reps=reps, base=base, stage=st))
+    return {"fwd": search(key, "fwd", fwd_candidates, path, force, lambda b, c: t("fwd", b, c)),
+            "bwd": search(key, "bwd", bwd_candidates, path, force, lambda b, c: t("bwd", b, c))}
 
 
-def search(key: str, candidates: Iterable[Tuple[int, int]], path: str, force: bool,
+def search(key: str, slot: str, candidates: Iterable[Tuple[int, int]], path: str, force: bool,
            timer) -> Tuple[int, int]:
-    """Cache lookup, else time every candidate and store the fastest."""
+    """Cache lookup of ``key``/``slot``, else time every candidate and store
+    the fastest."""
     if not force:
-        hit = _load(path).get(key)
+        hit = _load(path).get(key, {}).get(slot)
         if hit:
             return int(hit["batch"]), int(hit["ctas_per_sm"])
     results = {}
@@ -167,19 +186,22 @@ def search(key: str, candidates: Iterable[Tuple[int, int]], path: str, force: bo
         raise ValueError("no launch shape to try")
     best = min(results, key=results.get)
     b, c = (int(x) for x in best.split("x"))
-    _store(path, key, {"batch": b, "ctas_per_sm": c, "ms": results})
+    entry = _load(path).get(key, {})
+    entry[slot] = {"batch": b, "ctas_per_sm": c, "ms": results}
+    _store(path, key, entry)
     return b, c
 
 
 def config_for(scene, cams, base: Optional[abi.unigs_config] = None,
                cache_path: Optional[str] = None, tune_if_missing: bool = False):
-    """A ``unigs_config`` with the cached launch shape for this workload (the
-    library default when none is cached and ``tune_if_missing`` is false)."""
+    """A ``unigs_config`` with the cached launch shapes for this workload (the
+    library defaults for a stage without an entry, unless
+    ``tune_if_missing``)."""
     path = cache_path or default_cache_path()
-    hit = _load(path).get(workload_key(scene, cams))
-    if hit:
-        return make_config(hit["batch"], hit["ctas_per_sm"], base)
-    if tune_if_missing:
-        b, c = tune(scene, cams, base=base, cache_path=path)
-        return make_config(b, c, base)
-    return make_config(0, 0, base)
+    hit = _load(path).get(workload_key(scene, cams), {})
+    if tune_if_missing and not ("fwd" in hit and "bwd" in hit):
+        tune(scene, cams, base=base, cache_path=path)
+        hit = _load(path).get(workload_key(scene, cams), {})
+    f, b = hit.get("fwd", {}), hit.get("bwd", {})
+    return make_config(b.get("batch", 0), b.get("ctas_per_sm", 0), base,
+                       f.get("batch", 0), f.get("ctas_per_sm", 0))

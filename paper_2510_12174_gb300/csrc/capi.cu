@@ -87,6 +87,8 @@ void unigs_config_default(unigs_config* cfg) {
     cfg->flags = 0;
     cfg->batch = 0;
     cfg->ctas_per_sm = 0;
+    cfg->batch_fwd = 0;
+    cfg->ctas_per_sm_fwd = 0;
 }
 
 unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const unigs_camera* cams,
@@ -105,11 +107,17 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
         unigs_config_default(&plan->cfg);
     if (plan->cfg.step1 < 1 || plan->cfg.step1 > 4 || plan->cfg.step2 < 1 || plan->cfg.step2 > 4)
         return UNIGS_ERR_INVALID_ARG;
-    if (plan->cfg.flags & ~UNIGS_FLAG_CENTER_DEPTH) return UNIGS_ERR_INVALID_ARG;
+    if (plan->cfg.flags & ~(UNIGS_FLAG_CENTER_DEPTH | UNIGS_FLAG_SIMT_LOGITS))
+        return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.batch != 0 && plan->cfg.batch != 16 && plan->cfg.batch != 32 &&
         plan->cfg.batch != 64)
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.ctas_per_sm < 0 || plan->cfg.ctas_per_sm > 8) return UNIGS_ERR_INVALID_ARG;
+    if (plan->cfg.batch_fwd != 0 && plan->cfg.batch_fwd != 16 && plan->cfg.batch_fwd != 32 &&
+        plan->cfg.batch_fwd != 64)
+        return UNIGS_ERR_INVALID_ARG;
+    if (plan->cfg.ctas_per_sm_fwd < 0 || plan->cfg.ctas_per_sm_fwd > 8)
+        return UNIGS_ERR_INVALID_ARG;
     plan->n = g->n;
     plan->n_cams = n_cams;
     plan->n_sem = g->n_sem;

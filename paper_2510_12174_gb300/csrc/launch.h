@@ -12,6 +12,10 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
 int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st);
 int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_outputs& out, cudaStream_t st);
+// Tensor-core logit blend variant of the forward (bfloat16 logits, 9..64).
+bool fwd_tc_eligible(const unigs_plan& p, const unigs_gaussians& g);
+int launch_render_fwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws,
+                         const unigs_outputs& out, cudaStream_t st);
 int launch_depth_normal_fwd(const unigs_plan& p, const CamTable& tab, const float* depth,
                             float* normal_d, cudaStream_t st);
 int launch_depth_normal_bwd(const unigs_plan& p, const CamTable& tab, const float* depth,

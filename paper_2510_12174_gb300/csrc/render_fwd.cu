@@ -271,6 +271,7 @@ static void launch_fwd_b(const FwdParams& P, int grid, cudaStream_t st) {
 int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_outputs& out, cudaStream_t st) {
     if (p.n_tiles == 0) return 0;
+    if (fwd_tc_eligible(p, g)) return launch_render_fwd_tc(p, g, ws, out, st);
     FwdParams P;
     P.tab = ws_ptr<CamTable>(ws, p, OFF_CAM);
     P.n_cams = p.n_cams;
@@ -294,10 +295,13 @@ int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
     P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * 4) % 16 == 0) &&
                  ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
     cudaMemsetAsync(P.work, 0, sizeof(uint32_t), st);
-    const int ctas = p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 2;
+    // forward shape fields first, then the shared ones, then batch 32 x 2
+    const int ctas = p.cfg.ctas_per_sm_fwd > 0 ? p.cfg.ctas_per_sm_fwd
+                                               : (p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 2);
+    const int batch = p.cfg.batch_fwd > 0 ? p.cfg.batch_fwd : p.cfg.batch;
     int64_t grid = (int64_t)sm_count() * ctas;
     if (grid > p.n_tiles) grid = p.n_tiles;
-    switch (p.cfg.batch) {
+    switch (batch) {
         case 16: launch_fwd_b<16>(P, (int)grid, st); break;
         case 64: launch_fwd_b<64>(P, (int)grid, st); break;
         default: launch_fwd_b<32>(P, (int)grid, st); break;

@@ -26,31 +26,36 @@ def test_search_picks_fastest_and_caches(tmp_path):
         calls.append((b, c))
         return cost[(b, c)]
 
-    assert autotune.search("k", cost, path, False, timer) == (16, 2)
+    assert autotune.search("k", "bwd", cost, path, False, timer) == (16, 2)
     assert len(calls) == 3
     d = json.load(open(path))
-    assert d["k"]["batch"] == 16 and d["k"]["ms"]["64x1"] == 6.0
+    assert d["k"]["bwd"]["batch"] == 16 and d["k"]["bwd"]["ms"]["64x1"] == 6.0
     # a cached key is not timed again unless forced
-    assert autotune.search("k", cost, path, False, timer) == (16, 2)
+    assert autotune.search("k", "bwd", cost, path, False, timer) == (16, 2)
     assert len(calls) == 3
     cost[(64, 1)] = 1.0
-    assert autotune.search("k", cost, path, True, timer) == (64, 1)
-    # other keys are kept
-    autotune.search("other", {(32, 1): 1.0}, path, False, lambda b, c: 1.0)
-    assert set(json.load(open(path))) == {"k", "other"}
+    assert autotune.search("k", "bwd", cost, path, True, timer) == (64, 1)
+    # the other stage and other keys are kept
+    autotune.search("k", "fwd", {(16, 4): 1.0}, path, False, lambda b, c: 1.0)
+    autotune.search("other", "bwd", {(32, 1): 1.0}, path, False, lambda b, c: 1.0)
+    d = json.load(open(path))
+    assert set(d) == {"k", "other"} and set(d["k"]) == {"fwd", "bwd"}
+    assert d["k"]["bwd"]["batch"] == 64
 
 
 def test_search_rejects_invalid_shapes(tmp_path):
     with pytest.raises(ValueError):
-        autotune.search("k", [(48, 2)], str(tmp_path / "s.json"), False, lambda b, c: 1.0)
+        autotune.search("k", "fwd", [(48, 2)], str(tmp_path / "s.json"), False,
+                        lambda b, c: 1.0)
     with pytest.raises(ValueError):
-        autotune.search("k", [(32, 0)], str(tmp_path / "s.json"), False, lambda b, c: 1.0)
+        autotune.search("k", "fwd", [(32, 0)], str(tmp_path / "s.json"), False,
+                        lambda b, c: 1.0)
 
 
 def test_corrupt_cache_is_ignored(tmp_path):
     path = tmp_path / "s.json"
     path.write_text("{not json")
-    assert autotune.search("k", [(32, 2)], str(path), False, lambda b, c: 1.0) == (32, 2)
+    assert autotune.search("k", "bwd", [(32, 2)], str(path), False, lambda b, c: 1.0) == (32, 2)
 
 
 @pytest.mark.gpu
@@ -63,8 +68,10 @@ def test_tune_on_small_scene(tmp_path):
     sc, cams = scenes.small_room(n=4000, width=64, height=48, n_sem=16, seed=3, n_cams=2)
     ds = rz.DeviceScene.from_scene(sc)
     path = str(tmp_path / "s.json")
-    b, c = autotune.tune(ds, cams, candidates=[(32, 2), (16, 1)], reps=2, cache_path=path)
-    assert (b, c) in [(32, 2), (16, 1)]
+    best = autotune.tune(ds, cams, fwd_candidates=[(16, 4), (32, 2)],
+                         bwd_candidates=[(32, 2), (16, 1)], reps=2, cache_path=path)
+    assert best["fwd"] in [(16, 4), (32, 2)] and best["bwd"] in [(32, 2), (16, 1)]
     cfg = autotune.config_for(ds, cams, cache_path=path)
-    assert (cfg.batch, cfg.ctas_per_sm) == (b, c)
+    assert (cfg.batch, cfg.ctas_per_sm) == best["bwd"]
+    assert (cfg.batch_fwd, cfg.ctas_per_sm_fwd) == best["fwd"]
     torch.cuda.synchronize()

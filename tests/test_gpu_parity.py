@@ -82,6 +82,30 @@ def test_forward_parity_bf16_features():
     assert e["depth"] < TOL_REL and e["logits"] < TOL_REL
 
 
+@pytest.mark.parametrize("n_sem", [12, 32, 64])
+def test_tensor_core_logit_blend(n_sem):
+    """BF16 logits take the tensor-core blend (W F per tile batch, weights in
+    two bfloat16 parts): logits against the oracle at the forward tolerance and
+    against the FP32-pipe blend (UNIGS_FLAG_SIMT_LOGITS) within the split's
+    bound, |dO| <= 2^-18 sum_j w_j |f_j| plus float32 summation order, taken as
+    1e-5 max|f| (sum_j w_j <= 1); every other output is bit-identical."""
+    sc, cams = scenes.small_room(n=6000, width=70, height=50, n_sem=n_sem, seed=18,
+                                 feat_bf16=True, n_cams=2)
+    r_tc, o_tc = _render(sc, cams)
+    cfg = abi.unigs_config_default()
+    cfg.flags |= abi.UNIGS_FLAG_SIMT_LOGITS
+    r_s, o_s = _render(sc, cams, cfg=cfg)
+    for k in ("rgb", "depth", "normal_g", "kmap", "T_final", "n_contrib"):
+        assert torch.equal(o_tc[k], o_s[k]), k
+    a, b = o_tc["logits"], o_s["logits"]
+    fmax = float(np.abs(sc.sem).max())
+    assert float((a - b).abs().max()) < 1e-5 * fmax
+    _, ref, _ = oracle.render(sc, cams, with_normal_d=False)
+    e = forward_errors(r_tc, o_tc, ref, sc.n_sem)
+    print("tc", n_sem, e)
+    assert e["logits"] < TOL_REL
+
+
 def test_depth_normal_stage():
     """Alg. 1 on a seeded depth map (a tilted plane plus smooth bumps and
     noise), and Alg. 3 against the oracle's exact derivative."""
@@ -236,11 +260,12 @@ def test_autograd_function_matches_direct_backward():
         assert rel < 1e-3, (k, rel)
 
 
-@pytest.mark.parametrize("n", [1_000_000])
-def test_full_size_sampled_pixels(n):
+@pytest.mark.parametrize("bf16", [False, True])
+def test_full_size_sampled_pixels(bf16):
     """1M Gaussians at 1280x720 (the benchmark workload): binning bit-exact and
-    300 sampled pixels against the oracle."""
-    sc, cams = scenes.config3(n=n)
+    300 sampled pixels against the oracle; with BF16 features the logits come
+    from the tensor-core blend."""
+    sc, cams = scenes.config3(n=1_000_000, feat_bf16=bf16)
     r, out = _render(sc, cams)
     keys, vals, ranges = r.sorted_instances()
     ref = oracle.bin_cameras_fast(sc, cams)
