@@ -105,9 +105,9 @@ class ClockSampler:
 
 def launch_shape(cfg, simt_logits: bool) -> dict:
     """The composites' launch shapes after the library's defaults."""
-    bwd = (int(cfg.batch) or 32, int(cfg.ctas_per_sm) or 2)
+    bwd = (int(cfg.batch) or 8, int(cfg.ctas_per_sm) or 3)
     if simt_logits:
-        fwd = (int(cfg.batch_fwd) or bwd[0], int(cfg.ctas_per_sm_fwd) or bwd[1])
+        fwd = (int(cfg.batch_fwd) or 32, int(cfg.ctas_per_sm_fwd) or 2)
     else:
         fwd = (int(cfg.batch_fwd) or 16, min(int(cfg.ctas_per_sm_fwd) or 4, 4))
     return {"fwd": {"batch": fwd[0], "ctas_per_sm": fwd[1]},
@@ -581,7 +581,7 @@ def main():
     ap.add_argument("--train-gauss", type=int, default=6_000_000)
     ap.add_argument("--simt-logits", action="store_true",
                     help="blend the logits on the FP32 pipes instead of the tensor cores")
-    ap.add_argument("--batch", type=int, default=0, choices=[0, 16, 32, 64],
+    ap.add_argument("--batch", type=int, default=0, choices=[0, 8, 16, 32, 64],
                     help="Gaussians staged per batch by the composites (0: library default)")
     ap.add_argument("--ctas", type=int, default=0,
                     help="persistent composite CTAs per SM (0: library default)")

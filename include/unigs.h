@@ -149,14 +149,13 @@ typedef struct {
                              FP32 pipes even where the tensor-core blend
                              applies) */
     int32_t batch;        /* Gaussians staged per batch by the backward
-                             composite (and by the FP32-pipe forward when
-                             batch_fwd is 0): 16, 32 or 64 (0 = 32) */
-    int32_t ctas_per_sm;  /* persistent CTAs per SM, likewise, 1..8 (0 = 2) */
+                             composite: 8, 16, 32 or 64 (0 = 8) */
+    int32_t ctas_per_sm;  /* persistent backward CTAs per SM, 1..8 (0 = 3) */
     int32_t batch_fwd;    /* forward composite: 16, 32 or 64; 0 = 16 on the
-                             tensor-core path, else batch */
+                             tensor-core path, 32 on the FP32 pipes */
     int32_t ctas_per_sm_fwd; /* forward composite, 1..8 (the tensor-core path
-                             caps it at 4); 0 = 4 on the tensor-core path,
-                             else ctas_per_sm */
+                             caps it at 4); 0 = 4 on the tensor-core path, 2
+                             on the FP32 pipes */
 } unigs_config;
 
 #define UNIGS_FLAG_CENTER_DEPTH 1u

@@ -5,7 +5,8 @@ whose CTAs pull 16x16 tiles from a device work counter, longest Gaussian list
 first.  Two launch parameters per kernel change their speed but not their
 results:
 
-* the batch: Gaussians staged per shared-memory batch (16, 32 or 64).  Larger
+* the batch: Gaussians staged per shared-memory batch (8 - backward only -,
+  16, 32 or 64).  Larger
   batches amortise the barrier and bulk-copy issue per Gaussian; smaller ones
   waste less of the last batch of short lists and need less shared memory.
 * CTAs per SM (1-4): more CTAs hide barrier, MMA and atomic latency; fewer
@@ -39,7 +40,7 @@ from . import abi
 from . import rasterizer as rz
 
 FWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 4), (16, 3), (32, 2), (16, 2), (64, 2))
-BWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((32, 2), (16, 2), (64, 1), (32, 3), (16, 3))
+BWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((8, 3), (32, 2), (16, 2), (8, 2), (64, 1))
 
 
 def default_cache_path() -> str:
@@ -179,7 +180,7 @@ def search(key: str, slot: str, candidates: Iterable[Tuple[int, int]], path: str
             return int(hit["batch"]), int(hit["ctas_per_sm"])
     results = {}
     for b, c in candidates:
-        if b not in (16, 32, 64) or not 1 <= c <= 8:
+        if b not in ((8, 16, 32, 64) if slot == "bwd" else (16, 32, 64)) or not 1 <= c <= 8:
             raise ValueError(f"invalid launch shape ({b}, {c})")
         results[f"{b}x{c}"] = float(timer(b, c))
     if not results:

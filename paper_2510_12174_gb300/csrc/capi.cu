@@ -109,8 +109,8 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.flags & ~(UNIGS_FLAG_CENTER_DEPTH | UNIGS_FLAG_SIMT_LOGITS))
         return UNIGS_ERR_INVALID_ARG;
-    if (plan->cfg.batch != 0 && plan->cfg.batch != 16 && plan->cfg.batch != 32 &&
-        plan->cfg.batch != 64)
+    if (plan->cfg.batch != 0 && plan->cfg.batch != 8 && plan->cfg.batch != 16 &&
+        plan->cfg.batch != 32 && plan->cfg.batch != 64)
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.ctas_per_sm < 0 || plan->cfg.ctas_per_sm > 8) return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.batch_fwd != 0 && plan->cfg.batch_fwd != 16 && plan->cfg.batch_fwd != 32 &&

@@ -52,24 +52,32 @@ struct BwdParams {
 
 template <int NS, int B>
 struct BwdSmem {
-    static constexpr int GOP = NS + 4;  // padded pitch: row reads and column gathers
-                                        // both avoid bank conflicts
+    // dL/dlogits of the tile's pixels, one row of NS floats per thread; the
+    // 16-byte chunk k of row p is stored at chunk k ^ (p % (NS / 4)), so both
+    // the per-thread row reads and the per-row channel gathers of a warp are
+    // free of bank conflicts without padding
     float rec[2][B][REC_FLOATS];
     float sem[2][B][NS];
-    float gO[TILE_PIX][GOP];            // dL/dlogits of the tile's pixels, by thread
+    float gO[TILE_PIX * NS];
     uint32_t ids[2][B];
     uint64_t bar[2];
     uint32_t max_last;
     int tile;
 };
 
-// dot(gO row, semantic row) with 16-byte shared-memory loads.
+// Offset of channel c of pixel row p in the swizzled upstream-gradient tile.
 template <int NS>
-__device__ __forceinline__ float sem_dot(const float* go, const float* row) {
+__device__ __forceinline__ int go_index(int p, int c) {
+    return p * NS + ((((c >> 2) ^ p) & (NS / 4 - 1)) << 2) + (c & 3);
+}
+
+// dot(gO row p, semantic row) with 16-byte shared-memory loads.
+template <int NS>
+__device__ __forceinline__ float sem_dot(const float* go, int p, const float* row) {
     float acc = 0.f;
 #pragma unroll
     for (int c = 0; c < NS / 4; ++c) {
-        const float4 a = reinterpret_cast<const float4*>(go)[c];
+        const float4 a = *reinterpret_cast<const float4*>(go + go_index<NS>(p, 4 * c));
         const float4 b = reinterpret_cast<const float4*>(row)[c];
         acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
     }
@@ -105,7 +113,9 @@ __device__ __forceinline__ void cross_acc(const float* a, const float* b, float*
 }
 
 template <int NS, int B>
-__global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
+// batch 8 (71 KB of shared memory at 64 logits): 3 CTAs per SM, 80 registers;
+// larger batches (77 KB at 16, 90 KB at 32): 2 CTAs per SM, 128 registers
+__global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const BwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BwdSmem<NS, B>& S = *reinterpret_cast<BwdSmem<NS, B>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -154,8 +164,8 @@ __global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
         // upstream logit gradients of this pixel -> shared memory row tid (zero
         // padded), read by this thread for G_i and by the warp's channel gather
 #pragma unroll 8
-        for (int c = 0; c < BwdSmem<NS, B>::GOP; ++c)
-            S.gO[tid][c] = (inside && P.go.logits && c < P.n_sem)
+        for (int c = 0; c < NS; ++c)
+            S.gO[go_index<NS>(tid, c)] = (inside && P.go.logits && c < P.n_sem)
                                ? P.go.logits[pix * (int64_t)P.n_sem + c * HW + idx] : 0.f;
         if (inside) {
             T = P.T_final[pix + idx];
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
                         const float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
                                          g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
                                          sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
-                                         sem_dot<NS>(&S.gO[tid][0], &S.sem[buf][j][0]);
+                                         sem_dot<NS>(S.gO, tid, &S.sem[buf][j][0]);
                         const float dL_da = T * Gi - Sacc / om;
                         Sacc = fmaf(w, Gi, Sacc);
                         // alpha = min(alpha_max, op * Gs)
@@ -322,7 +332,10 @@ __global__ void __launch_bounds__(256, 2) render_bwd_kernel(const BwdParams P) {
                             m &= m - 1;
                             const float wl = __shfl_sync(0xffffffffu, w, l);
                             const float2 go =
-                                *reinterpret_cast<const float2*>(&S.gO[warp * 32 + l][2 * lane]);
+                                2 * lane < NS
+                                    ? *reinterpret_cast<const float2*>(
+                                          &S.gO[go_index<NS>(warp * 32 + l, 2 * lane)])
+                                    : make_float2(0.f, 0.f);
                             a0 = fmaf(wl, go.x, a0);
                             a1 = fmaf(wl, go.y, a1);
                         }
@@ -614,10 +627,13 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * 4) % 16 == 0) &&
                      ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
         cudaMemsetAsync(P.work, 0, sizeof(uint32_t), st);
-        const int ctas = p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 2;
+        // default shape: batch 8, 3 CTAs per SM
+        const int batch = p.cfg.batch > 0 ? p.cfg.batch : 8;
+        const int ctas = p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 3;
         int64_t grid = (int64_t)sm_count() * ctas;
         if (grid > p.n_tiles) grid = p.n_tiles;
-        switch (p.cfg.batch) {
+        switch (batch) {
+            case 8: launch_bwd_b<8>(P, (int)grid, st); break;
             case 16: launch_bwd_b<16>(P, (int)grid, st); break;
             case 64: launch_bwd_b<64>(P, (int)grid, st); break;
             default: launch_bwd_b<32>(P, (int)grid, st); break;

@@ -295,10 +295,9 @@ int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
     P.sem_bulk = (p.n_sem > 0) && ((p.n_sem * 4) % 16 == 0) &&
                  ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
     cudaMemsetAsync(P.work, 0, sizeof(uint32_t), st);
-    // forward shape fields first, then the shared ones, then batch 32 x 2
-    const int ctas = p.cfg.ctas_per_sm_fwd > 0 ? p.cfg.ctas_per_sm_fwd
-                                               : (p.cfg.ctas_per_sm > 0 ? p.cfg.ctas_per_sm : 2);
-    const int batch = p.cfg.batch_fwd > 0 ? p.cfg.batch_fwd : p.cfg.batch;
+    // forward shape fields, else batch 32 x 2 CTAs per SM
+    const int ctas = p.cfg.ctas_per_sm_fwd > 0 ? p.cfg.ctas_per_sm_fwd : 2;
+    const int batch = p.cfg.batch_fwd > 0 ? p.cfg.batch_fwd : 32;
     int64_t grid = (int64_t)sm_count() * ctas;
     if (grid > p.n_tiles) grid = p.n_tiles;
     switch (batch) {

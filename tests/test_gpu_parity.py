@@ -419,16 +419,18 @@ def test_full_size_finite_differences_64_params():
     print("FD 64 params: worst rel", worst)
 
 
-@pytest.mark.parametrize("batch,ctas", [(16, 1), (64, 2), (32, 3)])
+@pytest.mark.parametrize("batch,ctas", [(16, 1), (64, 2), (32, 3), (8, 2)])
 def test_launch_shape_invariance(batch, ctas):
     """The staged batch size and the number of persistent CTAs per SM change
     only the schedule: the forward is bit-identical to the default shape (each
-    pixel blends in the same order) and the gradients stay within tolerance of
-    the oracle (only the order of the float32 atomic additions moves)."""
+    pixel blends its list in the same order) and the gradients stay within
+    tolerance of the oracle (only the order of the float32 atomic additions
+    moves)."""
     sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=16, seed=27, n_cams=2)
     r0, o0 = _render(sc, cams)
     cfg = abi.unigs_config_default()
     cfg.batch, cfg.ctas_per_sm = batch, ctas
+    cfg.batch_fwd, cfg.ctas_per_sm_fwd = (batch if batch >= 16 else 16), ctas
     r1, o1 = _render(sc, cams, cfg=cfg)
     for k in o0:
         assert torch.equal(o0[k], o1[k]), k
