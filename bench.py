@@ -103,6 +103,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one render_bwd launch on this workload, from a
+# one-pass ncu capture of the full run (dram__bytes_read.sum 6.853 GB +
+# dram__bytes_write.sum 0.871 GB), valid only for the kernel sources whose
+# digest is recorded here; any change to them reports null until re-captured.
+BWD_TRAFFIC_BYTES = 7_723_292_416
+BWD_TRAFFIC_SOURCES = ("render_bwd.cu", "splat.cuh", "unigs_internal.cuh", "ff.cuh", "sh.cuh")
+BWD_TRAFFIC_DIGEST = "ad000462ef303f11cfed0d877bc2a08228760cf669ebdcb8873c36532ecee299"
+
+
+def bwd_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in BWD_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_12174_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return BWD_TRAFFIC_BYTES if h.hexdigest() == BWD_TRAFFIC_DIGEST else None
+
+
 def launch_shape(cfg, simt_logits: bool) -> dict:
     """The composites' launch shapes after the library's defaults."""
     bwd = (int(cfg.batch) or 8, int(cfg.ctas_per_sm) or 3)
@@ -372,7 +390,9 @@ def run_ours(args):
                  "gaussian_pixel_evals_per_s": n_eval / (ms_all / 1000.0)},
         "roofline": {"bound": "alu", "kernel": "render_bwd (composite backward + preprocess backward)",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak,
+                     "traffic": (bwd_traffic() if (args.n_gauss, args.batch, args.ctas) ==
+                                 (N_GAUSS, 0, 0) else None),
                      "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"},
         "e2e": {"value": N_VIEWS / (e2e_ms / 1000.0) * world, "unit": "views/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 64,

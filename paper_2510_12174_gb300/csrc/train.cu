@@ -46,13 +46,21 @@ __device__ __forceinline__ void pixel_cam(const LossParams& P, int64_t gp, int* 
 
 __device__ __forceinline__ float sgn(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
-// log-sum-exp and the logit of the label of one pixel (planar channels)
-__device__ __forceinline__ void pixel_lse(const float* O, int64_t hw, int C, float* mx_out,
-                                          float* z_out) {
+// The logits of one pixel (planar channels) into registers, padding with
+// -inf, and their maximum and sum of exponentials.
+template <int NS>
+__device__ __forceinline__ void pixel_logits(const float* O, int64_t hw, int C, float (&o)[NS],
+                                             float* mx_out, float* z_out) {
     float mx = -INFINITY;
-    for (int c = 0; c < C; ++c) mx = fmaxf(mx, O[(int64_t)c * hw]);
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+        o[c] = c < C ? O[(int64_t)c * hw] : -INFINITY;
+        mx = fmaxf(mx, o[c]);
+    }
     float z = 0.f;
-    for (int c = 0; c < C; ++c) z += expf(O[(int64_t)c * hw] - mx);
+#pragma unroll
+    for (int c = 0; c < NS; ++c)
+        if (c < C) z += expf(o[c] - mx);
     *mx_out = mx;
     *z_out = z;
 }
@@ -70,6 +78,7 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
     return s;  // valid in thread 0
 }
 
+template <int NS>
 __global__ void __launch_bounds__(LOSS_THREADS) loss_sums_kernel(const LossParams P) {
     __shared__ float sh[32];
     float acc[LOSS_SUMS] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -96,13 +105,17 @@ __global__ void __launch_bounds__(LOSS_THREADS) loss_sums_kernel(const LossParam
                 acc[3] += 1.f;
             }
         }
-        if (P.tgt.label && P.n_sem > 0) {
+        if (NS > 0 && P.tgt.label) {
             const int lab = P.tgt.label[gp];
             if (lab >= 0 && lab < P.n_sem) {
-                const float* O = P.logits + po * P.n_sem + idx;
-                float mx, z;
-                pixel_lse(O, hw, P.n_sem, &mx, &z);
-                acc[4] += mx + logf(z) - O[(int64_t)lab * hw];
+                constexpr int N1 = NS > 0 ? NS : 1;
+                float o[N1], mx, z;
+                pixel_logits<N1>(P.logits + po * P.n_sem + idx, hw, P.n_sem, o, &mx, &z);
+                float ol = 0.f;
+#pragma unroll
+                for (int c = 0; c < N1; ++c)
+                    if (c == lab) ol = o[c];
+                acc[4] += mx + logf(z) - ol;
                 acc[5] += 1.f;
             }
         }
@@ -156,6 +169,7 @@ __global__ void __launch_bounds__(LOSS_THREADS) loss_finalize_kernel(const LossP
     r[13] = r[14] = r[15] = 0.f;
 }
 
+template <int NS>
 __global__ void __launch_bounds__(LOSS_THREADS) loss_grad_kernel(const LossParams P) {
     const float* r = P.record;
     const float Pf = (float)P.n_pixels;
@@ -189,23 +203,34 @@ __global__ void __launch_bounds__(LOSS_THREADS) loss_grad_kernel(const LossParam
             P.g.depth[gp] = g;
         }
         if (P.g.kmap) P.g.kmap[gp] = P.kmap ? a_k * sgn(P.kmap[gp] - 1.f) : 0.f;
-        if (P.g.logits && P.n_sem > 0) {
+        if (NS > 0 && P.g.logits) {
+            constexpr int N1 = NS > 0 ? NS : 1;
             float* G = P.g.logits + po * P.n_sem + idx;
             const int lab = P.tgt.label ? P.tgt.label[gp] : -1;
             if (lab >= 0 && lab < P.n_sem) {
-                const float* O = P.logits + po * P.n_sem + idx;
-                float mx, z;
-                pixel_lse(O, hw, P.n_sem, &mx, &z);
+                float o[N1], mx, z;
+                pixel_logits<N1>(P.logits + po * P.n_sem + idx, hw, P.n_sem, o, &mx, &z);
                 const float iz = a_s / z;
-                for (int c = 0; c < P.n_sem; ++c) {
-                    const float p = expf(O[(int64_t)c * hw] - mx) * iz;
-                    G[(int64_t)c * hw] = c == lab ? p - a_s : p;
-                }
+#pragma unroll
+                for (int c = 0; c < N1; ++c)
+                    if (c < P.n_sem) {
+                        const float p = expf(o[c] - mx) * iz;
+                        G[(int64_t)c * hw] = c == lab ? p - a_s : p;
+                    }
             } else {
-                for (int c = 0; c < P.n_sem; ++c) G[(int64_t)c * hw] = 0.f;
+#pragma unroll
+                for (int c = 0; c < N1; ++c)
+                    if (c < P.n_sem) G[(int64_t)c * hw] = 0.f;
             }
         }
     }
+}
+
+template <int NS>
+static void launch_loss_t(const LossParams& P, int blocks, cudaStream_t st) {
+    loss_sums_kernel<NS><<<(unsigned)blocks, LOSS_THREADS, 0, st>>>(P);
+    loss_finalize_kernel<<<1, LOSS_THREADS, 0, st>>>(P, blocks);
+    loss_grad_kernel<NS><<<(unsigned)blocks, LOSS_THREADS, 0, st>>>(P);
 }
 
 int launch_loss(const unigs_plan& p, const unigs_outputs& out, const float* normal_d,
@@ -231,9 +256,18 @@ int launch_loss(const unigs_plan& p, const unigs_outputs& out, const float* norm
     if (blocks > cap) blocks = cap;
     if (blocks > LOSS_MAX_BLOCKS) blocks = LOSS_MAX_BLOCKS;
     if (blocks < 1) blocks = 1;
-    loss_sums_kernel<<<(unsigned)blocks, LOSS_THREADS, 0, st>>>(P);
-    loss_finalize_kernel<<<1, LOSS_THREADS, 0, st>>>(P, (int)blocks);
-    loss_grad_kernel<<<(unsigned)blocks, LOSS_THREADS, 0, st>>>(P);
+    // logits of a pixel are held in registers: the kernels are compiled for
+    // 8, 16, 32 and 64 channels
+    if (p.n_sem == 0)
+        launch_loss_t<0>(P, (int)blocks, st);
+    else if (p.n_sem <= 8)
+        launch_loss_t<8>(P, (int)blocks, st);
+    else if (p.n_sem <= 16)
+        launch_loss_t<16>(P, (int)blocks, st);
+    else if (p.n_sem <= 32)
+        launch_loss_t<32>(P, (int)blocks, st);
+    else
+        launch_loss_t<64>(P, (int)blocks, st);
     return 3;
 }
 
@@ -245,6 +279,31 @@ struct AdamParams {
     const int32_t* step;
 };
 
+// One element of the update (or, without UPDATE, of the copies only).
+template <bool UPDATE>
+__device__ __forceinline__ float adam_one(float raw, float g, float& m, float& v, int act,
+                                          float lr, float b1, float b2, float eps, float bc1,
+                                          float bc2) {
+    if (UPDATE) {
+        if (act == UNIGS_ACT_EXP) {
+            g *= expf(raw);
+        } else if (act == UNIGS_ACT_SIGMOID) {
+            const float s = 1.f / (1.f + expf(-raw));
+            g *= s * (1.f - s);
+        }
+        m = b1 * m + (1.f - b1) * g;
+        v = b2 * v + (1.f - b2) * g * g;
+        raw -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    }
+    return raw;
+}
+
+__device__ __forceinline__ float activate(float raw, int act) {
+    if (act == UNIGS_ACT_EXP) return expf(raw);
+    if (act == UNIGS_ACT_SIGMOID) return 1.f / (1.f + expf(-raw));
+    return raw;
+}
+
 template <bool UPDATE>
 __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamParams P) {
     const unigs_adam_group& G = P.grp[blockIdx.y];
@@ -253,27 +312,61 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
     const float bc2 = 1.f - powf(P.beta2, (float)t);
     const float lr = G.lr;
     const int act = G.activation;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float raw = G.param[i];
+    const float b1 = P.beta1, b2 = P.beta2, eps = P.eps;
+    // 16-byte vectors where every array allows it (bfloat16 copies: 8 bytes)
+    const uintptr_t al = reinterpret_cast<uintptr_t>(G.param) |
+                         (UPDATE ? reinterpret_cast<uintptr_t>(G.grad) |
+                                       reinterpret_cast<uintptr_t>(G.m) |
+                                       reinterpret_cast<uintptr_t>(G.v)
+                                 : 0) |
+                         reinterpret_cast<uintptr_t>(G.act_out);
+    const bool vec = (al & 15) == 0 && (reinterpret_cast<uintptr_t>(G.bf16_out) & 7) == 0;
+    const int64_t n4 = vec ? G.count / 4 : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 raw = reinterpret_cast<const float4*>(G.param)[i];
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f), m = g, v = g;
         if (UPDATE) {
-            float g = G.grad[i];
-            if (act == UNIGS_ACT_EXP) {
-                g *= expf(raw);
-            } else if (act == UNIGS_ACT_SIGMOID) {
-                const float s = 1.f / (1.f + expf(-raw));
-                g *= s * (1.f - s);
-            }
-            const float m = P.beta1 * G.m[i] + (1.f - P.beta1) * g;
-            const float v = P.beta2 * G.v[i] + (1.f - P.beta2) * g * g;
+            g = reinterpret_cast<const float4*>(G.grad)[i];
+            m = reinterpret_cast<const float4*>(G.m)[i];
+            v = reinterpret_cast<const float4*>(G.v)[i];
+        }
+        raw.x = adam_one<UPDATE>(raw.x, g.x, m.x, v.x, act, lr, b1, b2, eps, bc1, bc2);
+        raw.y = adam_one<UPDATE>(raw.y, g.y, m.y, v.y, act, lr, b1, b2, eps, bc1, bc2);
+        raw.z = adam_one<UPDATE>(raw.z, g.z, m.z, v.z, act, lr, b1, b2, eps, bc1, bc2);
+        raw.w = adam_one<UPDATE>(raw.w, g.w, m.w, v.w, act, lr, b1, b2, eps, bc1, bc2);
+        if (UPDATE) {
+            reinterpret_cast<float4*>(G.param)[i] = raw;
+            reinterpret_cast<float4*>(G.m)[i] = m;
+            reinterpret_cast<float4*>(G.v)[i] = v;
+        }
+        const float4 a = make_float4(activate(raw.x, act), activate(raw.y, act),
+                                     activate(raw.z, act), activate(raw.w, act));
+        if (G.act_out) reinterpret_cast<float4*>(G.act_out)[i] = a;
+        if (G.bf16_out) {
+            const uint32_t lo = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a.x)) |
+                                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a.y)) << 16);
+            const uint32_t hi = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a.z)) |
+                                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a.w)) << 16);
+            reinterpret_cast<uint2*>(G.bf16_out)[i] = make_uint2(lo, hi);
+        }
+    }
+    // scalar elements (the tail, or everything without vector alignment)
+    for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.count;
+         i += stride) {
+        float m = 0.f, v = 0.f, g = 0.f;
+        if (UPDATE) {
+            g = G.grad[i];
+            m = G.m[i];
+            v = G.v[i];
+        }
+        const float raw = adam_one<UPDATE>(G.param[i], g, m, v, act, lr, b1, b2, eps, bc1, bc2);
+        if (UPDATE) {
+            G.param[i] = raw;
             G.m[i] = m;
             G.v[i] = v;
-            raw -= lr * (m / bc1) / (sqrtf(v / bc2) + P.eps);
-            G.param[i] = raw;
         }
-        float a = raw;
-        if (act == UNIGS_ACT_EXP) a = expf(raw);
-        else if (act == UNIGS_ACT_SIGMOID) a = 1.f / (1.f + expf(-raw));
+        const float a = activate(raw, act);
         if (G.act_out) G.act_out[i] = a;
         if (G.bf16_out) reinterpret_cast<__nv_bfloat16*>(G.bf16_out)[i] = __float2bfloat16_rn(a);
     }
@@ -298,7 +391,7 @@ static AdamParams adam_params(const unigs_adam_group* groups, int n_groups,
 }
 
 static unsigned adam_blocks(int64_t most) {
-    int64_t bx = (most + 255) / 256;
+    int64_t bx = (most / 4 + 255) / 256 + 1;
     const int64_t cap = (int64_t)sm_count() * 8;
     return (unsigned)(bx > cap ? cap : bx);
 }
