@@ -55,7 +55,8 @@ def render(scene, cams, requires_grad: bool = False, binning=None,
 
 
 def render_and_grad(scene, cams, upstream: Dict[str, List[np.ndarray]],
-                    binning=None, bands: Optional[Bands] = None, center_depth: bool = False):
+                    binning=None, bands: Optional[Bands] = None, center_depth: bool = False,
+                    tiles: Optional[Sequence[Sequence[int]]] = None):
     """Forward plus exact gradients of L = sum_c <output_c, upstream_c>.
 
     ``upstream`` maps rgb, depth, normal_g, kmap, logits, normal_d to per-camera
@@ -63,7 +64,7 @@ def render_and_grad(scene, cams, upstream: Dict[str, List[np.ndarray]],
     grads keyed like the Gaussian parameters.
     """
     params, outs, binning = render(scene, cams, requires_grad=True, binning=binning,
-                                   bands=bands, center_depth=center_depth)
+                                   bands=bands, center_depth=center_depth, tiles=tiles)
     loss = torch.zeros((), dtype=torch.float64)
     name = {"rgb": "rgb", "depth": "depth", "normal_g": "normal", "kmap": "kmap",
             "logits": "logits", "normal_d": "normal_d"}

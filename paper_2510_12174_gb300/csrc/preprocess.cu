@@ -368,6 +368,10 @@ __global__ void __launch_bounds__(256)
             for (int b = 0; b < 3; ++b) o[R_NW + a * 3 + b] = rc.R[a][b] * is[b];
         }
         o[R_Z] = rc.pz;
+        o[R_KAP + 0] = rc.pz * sx / (sy * sz);
+        o[R_KAP + 1] = rc.pz * sy / (sx * sz);
+        o[R_KAP + 2] = rc.pz * sz / (sx * sy);
+        o[43] = 0.f;
         {
             // box of the q <= qlim ellipse (x half-extent sqrt(qlim * Sigma_xx)),
             // with a relative and a one-pixel margin

@@ -79,12 +79,23 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 //   p_mid = (d_s x cv)/a (closest approach), h = sqrt(disc)/a (0 on a miss),
 //   p = p_mid - sr h d_s (entry point; exit point when the camera is inside,
 //   sr = -1), normal n = sign * normalize(N_w p).
+// cv is not formed as v_s x d_s: for a Gaussian far from the camera |v_s| is
+// hundreds and the product cancels to the ray's offset from the centre, so
+// the float32 rounding of v_s (a few ulp of |v_s|) would move the silhouette
+// and the normal.  With v_s = -S^-1 Q p_c, d_s = S^-1 Q d~ (Q = R^T R_cw,
+// M_c = S^-1 Q) and p_c = z m~ (m~ = the centre's ray, m~_z = 1):
+//   v_s x d_s = det(S^-1) S Q (d~ x p_c) = kappa (.) M_c (Delta x m~),
+// Delta = d~ - m~ = ((u - m_x)/fx, (v - m_y)/fy, 0) from the exactly formed
+// pixel offset of the splat, kappa_a = z s_a / (s_b s_c): no cancellation.
 struct PairGeom {
     float ds[3], a, bp, t, cv[3], disc, pm[3], h, p[3], m[3], inv_m, sr;
     bool hit, inside;
 };
 
+// dxp, dyp: the pixel offset from the projected centre (splat_alpha's
+// outputs); ifx, ify: 1/fx, 1/fy.
 __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, float xt, float yt,
+                                              float dxp, float dyp, float ifx, float ify,
                                               PairGeom& G) {
     const float* M = rc + R_MC;
     const float* vs = rc + R_VS;
@@ -94,9 +105,13 @@ __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, floa
     G.bp = fmaf(vs[0], G.ds[0], fmaf(vs[1], G.ds[1], vs[2] * G.ds[2]));
     const float inv_a = 1.f / G.a;
     G.t = -G.bp * inv_a;
-    G.cv[0] = diff_of_products(vs[1], G.ds[2], vs[2], G.ds[1]);
-    G.cv[1] = diff_of_products(vs[2], G.ds[0], vs[0], G.ds[2]);
-    G.cv[2] = diff_of_products(vs[0], G.ds[1], vs[1], G.ds[0]);
+    {
+        const float Dx = dxp * ifx, Dy = dyp * ify;
+        const float w0 = Dy, w1 = -Dx, w2 = fmaf(Dx, yt, -Dy * xt);  // Delta x m~
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            G.cv[i] = rc[R_KAP + i] * fmaf(M[3 * i], w0, fmaf(M[3 * i + 1], w1, M[3 * i + 2] * w2));
+    }
     const float cc = fmaf(G.cv[0], G.cv[0], fmaf(G.cv[1], G.cv[1], G.cv[2] * G.cv[2]));
     G.disc = G.a - cc;
     G.pm[0] = diff_of_products(G.ds[1], G.cv[2], G.ds[2], G.cv[1]) * inv_a;

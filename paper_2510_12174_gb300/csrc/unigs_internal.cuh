@@ -14,7 +14,7 @@ constexpr int TILE_PIX = TILE * TILE;
 
 // ----------------------------------------------------------------------------
 // Per-(camera, Gaussian) forward record written by the preprocess and staged
-// into shared memory by the composite kernels (40 floats = 160 bytes, a
+// into shared memory by the composite kernels (44 floats = 176 bytes, a
 // multiple of 16 so a bulk copy can move it).
 //   [0..3]  projected centre split as integer part + remainder (x_hi, y_hi,
 //           x_lo, y_lo); m = hi + lo, hi an integer-valued float, |lo| <= 0.5
@@ -30,11 +30,15 @@ constexpr int TILE_PIX = TILE * TILE;
 //   [38..39] half-extents (x, y) of the box holding every pixel where alpha
 //           can reach alpha_min (with margin): a warp whose 8x4 pixel block
 //           lies outside skips the Gaussian
+//   [40..42] kappa_a = z s_a / (s_b s_c): v_s x d_s = kappa (.) M_c (Delta x m~)
+//           (see pair_geometry), the cancellation-free form of the cross
+//           product for Gaussians far from the camera
+//   [43]    unused
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_OP, R_K, R_RGB, R_CON = 9, R_MC = 12,
     R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34, R_FLAG = 37, R_EXTX = 38, R_EXTY = 39,
-    REC_FLOATS = 40
+    R_KAP = 40, REC_FLOATS = 44
 };
 
 // Pixel of thread tid inside its 16x16 tile: warp w covers the 8x4 block at
