@@ -10,9 +10,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "unigs.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(unigs_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(unigs_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +30,9 @@ def lib():
 def test_header_declares_entry_points():
     names = _declared()
     for n in ("unigs_preprocess", "unigs_bin_sort", "unigs_render_fwd", "unigs_render_bwd",
-              "unigs_depth_normal_fwd", "unigs_depth_normal_bwd", "unigs_plan_init"):
+              "unigs_depth_normal_fwd", "unigs_depth_normal_bwd", "unigs_plan_init",
+              "unigs_loss", "unigs_adam_step", "unigs_param_copies", "unigs_prune_mark",
+              "unigs_prune_compact", "unigs_sort_pairs_static"):
         assert n in names
 
 
@@ -80,3 +86,75 @@ def test_multi_camera_plan_offsets(lib):
     assert list(plan.tile_offset[:4]) == [0, t[0], t[0] + t[1], sum(t)]
     assert list(plan.pixel_offset[:4]) == [0, 307200, 307200 + 921600, 307200 + 921600 + 2073600]
     assert plan.capacity == 4 * 100 * 3
+
+
+def test_training_entry_points_check_arguments_on_host(lib):
+    """The training entry points refuse bad arguments before any launch."""
+    import ctypes
+    from paper_2510_12174_gb300 import rasterizer as rz, scenes
+    L = lib.lib()
+    lam = lib.unigs_loss_lambda()
+    L.unigs_loss_lambda_default(ctypes.byref(lam))
+    assert (lam.l1, round(lam.normal, 6), round(lam.depth, 6), round(lam.seg, 6),
+            round(lam.K, 6)) == (1.0, 0.1, 0.1, 0.1, 0.1)
+    sc, cams = scenes.small_room(n=10, width=20, height=20)
+    g = lib.unigs_gaussians()
+    g.n, g.sh_degree, g.n_sem, g.feat_dtype = 10, 3, 8, 0
+    plan = lib.unigs_plan()
+    assert lib.unigs_plan_init(plan, g, rz.make_cameras(cams), 1, None, 0) == lib.UNIGS_OK
+    out = lib.unigs_outputs()
+    tgt = lib.unigs_targets()
+    grads = lib.unigs_loss_grads()
+    args = (ctypes.byref(plan), ctypes.byref(out), None, ctypes.byref(tgt), ctypes.byref(lam))
+    # no record
+    assert L.unigs_loss(*args, 16, None, ctypes.byref(grads), None) == lib.UNIGS_ERR_INVALID_ARG
+    # a target without its output
+    tgt.rgb = 16
+    assert L.unigs_loss(*args, 16, 16, ctypes.byref(grads), None) == lib.UNIGS_ERR_INVALID_ARG
+    tgt.rgb = None
+    tgt.normal = 16                      # normal target without the normal-from-depth map
+    assert L.unigs_loss(*args, 16, 16, ctypes.byref(grads), None) == lib.UNIGS_ERR_INVALID_ARG
+    # Adam: too many groups, a bad activation, an activated copy over the raw values
+    hp = lib.unigs_adam_hparams(0.9, 0.999, 1e-15)
+    groups = (lib.unigs_adam_group * 1)()
+    assert L.unigs_adam_step(groups, 17, ctypes.byref(hp), 16, None) == lib.UNIGS_ERR_INVALID_ARG
+    G = groups[0]
+    G.param, G.grad, G.m, G.v, G.count = 16, 32, 48, 64, 4
+    G.activation = 3
+    assert L.unigs_adam_step(groups, 1, ctypes.byref(hp), 16, None) == lib.UNIGS_ERR_INVALID_ARG
+    G.activation = lib.UNIGS_ACT_EXP
+    G.act_out = 16
+    assert L.unigs_adam_step(groups, 1, ctypes.byref(hp), 16, None) == lib.UNIGS_ERR_INVALID_ARG
+    assert L.unigs_param_copies(groups, 1, None) == lib.UNIGS_ERR_INVALID_ARG
+    G.act_out, G.m = None, None          # missing moment
+    assert L.unigs_adam_step(groups, 1, ctypes.byref(hp), 16, None) == lib.UNIGS_ERR_INVALID_ARG
+    assert L.unigs_adam_step(groups, 1, ctypes.byref(hp), None, None) == lib.UNIGS_ERR_INVALID_ARG
+    # pruning: workspace size grows with n; bad sizes, aliasing, fill of 2-byte elements
+    assert L.unigs_prune_workspace_bytes(1000) > L.unigs_prune_workspace_bytes(10) > 0
+    nk = ctypes.c_int64(0)
+    assert L.unigs_prune_mark(16, -1, 0.2, 16, ctypes.byref(nk), None) == lib.UNIGS_ERR_INVALID_ARG
+    assert L.unigs_prune_mark(16, 10, 0.2, 8, ctypes.byref(nk), None) == lib.UNIGS_ERR_INVALID_ARG
+    arr = (lib.unigs_prune_array * 1)()
+    arr[0].src, arr[0].dst, arr[0].planes, arr[0].row, arr[0].elem_bytes = 16, 16, 1, 1, 4
+    assert L.unigs_prune_compact(arr, 1, 10, 5, 16, None) == lib.UNIGS_ERR_INVALID_ARG
+    arr[0].dst, arr[0].elem_bytes, arr[0].fill = 32, 2, 1
+    assert L.unigs_prune_compact(arr, 1, 10, 5, 16, None) == lib.UNIGS_ERR_INVALID_ARG
+    arr[0].elem_bytes, arr[0].fill = 4, 0
+    assert L.unigs_prune_compact(arr, 1, 10, 11, 16, None) == lib.UNIGS_ERR_INVALID_ARG
+
+
+def test_launch_shape_fields_are_validated(lib):
+    from paper_2510_12174_gb300 import rasterizer as rz, scenes
+    sc, cams = scenes.small_room(n=10, width=20, height=20)
+    g = lib.unigs_gaussians()
+    g.n, g.sh_degree, g.n_sem, g.feat_dtype = 10, 3, 8, 1
+    plan = lib.unigs_plan()
+    arr = rz.make_cameras(cams)
+    for field, value, ok in (("batch", 8, True), ("batch", 48, False), ("batch_fwd", 8, False),
+                             ("batch_fwd", 64, True), ("ctas_per_sm", 9, False),
+                             ("ctas_per_sm_fwd", 4, True), ("flags", 4, False),
+                             ("flags", 3, True)):
+        cfg = lib.unigs_config_default()
+        setattr(cfg, field, value)
+        want = lib.UNIGS_OK if ok else lib.UNIGS_ERR_INVALID_ARG
+        assert lib.unigs_plan_init(plan, g, arr, 1, cfg, 0) == want, (field, value)
