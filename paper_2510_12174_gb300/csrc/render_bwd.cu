@@ -59,6 +59,7 @@ struct BwdSmem {
     float rec[2][B][REC_FLOATS];
     float sem[2][B][NS];
     float gO[TILE_PIX * NS];
+    float wv[8][32];  // per warp: the weights w of its pixels for the current Gaussian
     uint32_t ids[2][B];
     uint64_t bar[2];
     uint32_t max_last;
@@ -324,8 +325,48 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                     const float tot = warp_reduce_transpose32(gv, lane);
                     if (tot != 0.f) atomicAdd(P.grec + rix * GREC_FLOATS + lane, tot);
                     if (P.n_sem > 0) {
-                        // dL/do_j[c] = sum over the contributing pixels l of w_l gO_l[c]:
-                        // lane L gathers channels 2L, 2L+1 (w_l by shuffle)
+                        // dL/do_j[c] = sum over the contributing pixels l of w_l gO_l[c]
+                        if (NS == 64 && __popc(cmask) > 12) {
+                            // many contributors: every row, two at a time, lanes
+                            // 16 h .. 16 h + 15 take row 2 i + h and channels
+                            // 4 (lane % 16) .. + 3 (16-byte loads), then the
+                            // halves are added
+                            S.wv[warp][lane] = w;
+                            __syncwarp();
+                            const int h = lane >> 4, c4 = lane & 15;
+                            const float* rowbase = S.gO + (warp * 32 + h) * NS;
+                            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const int r = 2 * i + h;
+                                const float wr = S.wv[warp][r];
+                                const float4 go = *reinterpret_cast<const float4*>(
+                                    rowbase + 2 * i * NS + ((c4 ^ (r & 15)) << 2));
+                                acc.x = fmaf(wr, go.x, acc.x);
+                                acc.y = fmaf(wr, go.y, acc.y);
+                                acc.z = fmaf(wr, go.z, acc.z);
+                                acc.w = fmaf(wr, go.w, acc.w);
+                            }
+                            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+                            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+                            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 16);
+                            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 16);
+                            __syncwarp();
+                            const int c = 4 * c4;
+                            if (h == 0 && c < P.n_sem) {
+                                float* dst = P.gsem + (size_t)g * P.n_sem + c;
+                                if ((P.n_sem & 3) == 0) {
+                                    atomicAdd(reinterpret_cast<float4*>(dst), acc);
+                                } else {
+                                    const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+                                    for (int e = 0; e < 4 && c + e < P.n_sem; ++e)
+                                        atomicAdd(dst + e, av[e]);
+                                }
+                            }
+                            continue;
+                        }
+                        // few contributors: lane L gathers channels 2L, 2L+1 over
+                        // the contributing pixels (w_l by shuffle)
                         float a0 = 0.f, a1 = 0.f;
                         unsigned m = cmask;
                         while (m) {
