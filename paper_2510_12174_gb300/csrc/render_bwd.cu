@@ -27,6 +27,7 @@ namespace unigs {
 
 constexpr uint32_t BWAIT_LIMIT = 1u << 22;
 
+
 struct BwdParams {
     const CamTable* tab;
     int n_cams;
@@ -326,31 +327,36 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                     if (tot != 0.f) atomicAdd(P.grec + rix * GREC_FLOATS + lane, tot);
                     if (P.n_sem > 0) {
                         // dL/do_j[c] = sum over the contributing pixels l of w_l gO_l[c]
-                        if (NS == 64 && __popc(cmask) > 12) {
-                            // many contributors: every row, two at a time, lanes
-                            // 16 h .. 16 h + 15 take row 2 i + h and channels
-                            // 4 (lane % 16) .. + 3 (16-byte loads), then the
-                            // halves are added
+                        {
+                            // every row of the warp (w = 0 where the pixel does not
+                            // contribute), NS/4 lanes per row (16-byte loads of 4
+                            // channels), 128/NS rows per step; the lanes that share
+                            // channels are then added.  Cheaper than looping over the
+                            // contributing lanes only: most warps have many.
+                            constexpr int LPR = NS / 4, RPS = 32 / LPR;
                             S.wv[warp][lane] = w;
                             __syncwarp();
-                            const int h = lane >> 4, c4 = lane & 15;
+                            const int h = lane / LPR, c4 = lane % LPR;
                             const float* rowbase = S.gO + (warp * 32 + h) * NS;
                             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const int r = 2 * i + h;
+                            for (int i = 0; i < LPR; ++i) {
+                                const int r = i * RPS + h;
                                 const float wr = S.wv[warp][r];
                                 const float4 go = *reinterpret_cast<const float4*>(
-                                    rowbase + 2 * i * NS + ((c4 ^ (r & 15)) << 2));
+                                    rowbase + i * RPS * NS + ((c4 ^ (r & (LPR - 1))) << 2));
                                 acc.x = fmaf(wr, go.x, acc.x);
                                 acc.y = fmaf(wr, go.y, acc.y);
                                 acc.z = fmaf(wr, go.z, acc.z);
                                 acc.w = fmaf(wr, go.w, acc.w);
                             }
-                            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-                            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-                            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 16);
-                            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 16);
+#pragma unroll
+                            for (int o = LPR; o < 32; o <<= 1) {
+                                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                                acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+                                acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+                            }
                             __syncwarp();
                             const int c = 4 * c4;
                             if (h == 0 && c < P.n_sem) {
@@ -363,32 +369,6 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                                         atomicAdd(dst + e, av[e]);
                                 }
                             }
-                            continue;
-                        }
-                        // few contributors: lane L gathers channels 2L, 2L+1 over
-                        // the contributing pixels (w_l by shuffle)
-                        float a0 = 0.f, a1 = 0.f;
-                        unsigned m = cmask;
-                        while (m) {
-                            const int l = __ffs(m) - 1;
-                            m &= m - 1;
-                            const float wl = __shfl_sync(0xffffffffu, w, l);
-                            const float2 go =
-                                2 * lane < NS
-                                    ? *reinterpret_cast<const float2*>(
-                                          &S.gO[go_index<NS>(warp * 32 + l, 2 * lane)])
-                                    : make_float2(0.f, 0.f);
-                            a0 = fmaf(wl, go.x, a0);
-                            a1 = fmaf(wl, go.y, a1);
-                        }
-                        const int c = 2 * lane;
-                        float* dst = P.gsem + (size_t)g * P.n_sem + c;
-                        if (c + 1 < P.n_sem && (P.n_sem & 1) == 0) {
-                            if (a0 != 0.f || a1 != 0.f)
-                                atomicAdd(reinterpret_cast<float2*>(dst), make_float2(a0, a1));
-                        } else {
-                            if (c < P.n_sem && a0 != 0.f) atomicAdd(dst, a0);
-                            if (c + 1 < P.n_sem && a1 != 0.f) atomicAdd(dst + 1, a1);
                         }
                     }
                 }
