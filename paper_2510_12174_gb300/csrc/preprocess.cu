@@ -371,7 +371,11 @@ __global__ void __launch_bounds__(256)
         o[R_KAP + 0] = rc.pz * sx / (sy * sz);
         o[R_KAP + 1] = rc.pz * sy / (sx * sz);
         o[R_KAP + 2] = rc.pz * sz / (sx * sy);
-        o[43] = 0.f;
+        {
+            const float* v = o + R_VS;
+            const float vv = fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2]));
+            o[R_SR] = vv <= 1.f ? -1.f : 1.f;
+        }
         {
             // box of the q <= qlim ellipse (x half-extent sqrt(qlim * Sigma_xx)),
             // with a relative and a one-pixel margin

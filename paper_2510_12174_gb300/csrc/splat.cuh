@@ -114,12 +114,13 @@ __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, floa
     }
     const float cc = fmaf(G.cv[0], G.cv[0], fmaf(G.cv[1], G.cv[1], G.cv[2] * G.cv[2]));
     G.disc = G.a - cc;
-    G.pm[0] = diff_of_products(G.ds[1], G.cv[2], G.ds[2], G.cv[1]) * inv_a;
-    G.pm[1] = diff_of_products(G.ds[2], G.cv[0], G.ds[0], G.cv[2]) * inv_a;
-    G.pm[2] = diff_of_products(G.ds[0], G.cv[1], G.ds[1], G.cv[0]) * inv_a;
-    const float vv = fmaf(vs[0], vs[0], fmaf(vs[1], vs[1], vs[2] * vs[2]));
-    G.inside = vv <= 1.f;
-    G.sr = G.inside ? -1.f : 1.f;
+    // d_s and cv are orthogonal, so the cross product does not cancel
+    G.pm[0] = fmaf(G.ds[1], G.cv[2], -G.ds[2] * G.cv[1]) * inv_a;
+    G.pm[1] = fmaf(G.ds[2], G.cv[0], -G.ds[0] * G.cv[2]) * inv_a;
+    G.pm[2] = fmaf(G.ds[0], G.cv[1], -G.ds[1] * G.cv[0]) * inv_a;
+    // camera inside the 1-sigma ellipsoid (|v_s| <= 1): a per-Gaussian sign
+    G.sr = rc[R_SR];
+    G.inside = G.sr < 0.f;
     G.hit = G.disc > 0.f;
     G.h = G.hit ? sqrtf(G.disc) * inv_a : 0.f;
 #pragma unroll

@@ -33,12 +33,13 @@ constexpr int TILE_PIX = TILE * TILE;
 //   [40..42] kappa_a = z s_a / (s_b s_c): v_s x d_s = kappa (.) M_c (Delta x m~)
 //           (see pair_geometry), the cancellation-free form of the cross
 //           product for Gaussians far from the camera
-//   [43]    unused
+//   [43]    -1 when the camera is inside the 1-sigma ellipsoid (|v_s| <= 1),
+//           else +1
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_OP, R_K, R_RGB, R_CON = 9, R_MC = 12,
     R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34, R_FLAG = 37, R_EXTX = 38, R_EXTY = 39,
-    R_KAP = 40, REC_FLOATS = 44
+    R_KAP = 40, R_SR = 43, REC_FLOATS = 44
 };
 
 // Pixel of thread tid inside its 16x16 tile: warp w covers the 8x4 block at
