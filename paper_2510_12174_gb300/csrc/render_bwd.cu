@@ -1,7 +1,8 @@
 // Backward composite (Alg. 4) and preprocess backward.
 //
-// Kernel 1, one CTA per tile: each pixel restores T = T_final and walks its
-// list backwards from the last blended Gaussian, T <- T / (1 - alpha_i),
+// Kernel 1, persistent CTAs pulling 16x16 tiles longest list first, one pixel
+// per thread: each pixel restores T = T_final and walks its list backwards
+// from the last blended Gaussian, T <- T / (1 - alpha_i),
 // w_i = alpha_i T_i.  With G_i = sum_ch g_ch x_i,ch (upstream gradient dotted
 // with the Gaussian's features) and S_i = sum_{j>i} w_j G_j,
 //   dL/dx_i,ch = w_i g_ch            (Eq. gradiento, Eq. gradientk)
@@ -11,7 +12,11 @@
 // normal flow to the per-(camera, Gaussian) ray-ellipsoid setup (M_c, v_s,
 // N_w); dL/dalpha flows to opacity, conic and projected centre.  The 32
 // lanes of a warp (32 pixels) are summed with a butterfly transpose-reduction
-// (lane L ends with component L) before one float32 atomic per lane.
+// (lane L ends with component L) before one float32 atomic per lane.  The
+// semantic gradients sum_l w_l g_O,l of the warp's 32 pixels are gathered
+// densely from the tile's upstream-gradient rows in shared memory (4 channels
+// per 16-byte load, w = 0 for pixels that do not contribute), one 16-byte
+// atomic per 4 channels.
 //
 // Kernel 2, one thread per Gaussian, loops over the cameras: conic -> 2D
 // covariance -> (J, Sigma) -> mean, rotation, scale (EWA chain of 3DGS);
