@@ -15,31 +15,35 @@ constexpr int TILE_PIX = TILE * TILE;
 // ----------------------------------------------------------------------------
 // Per-(camera, Gaussian) forward record written by the preprocess and staged
 // into shared memory by the composite kernels (44 floats = 176 bytes, a
-// multiple of 16 so a bulk copy can move it).
+// multiple of 16 so a bulk copy can move it).  The fields every evaluated
+// (pixel, Gaussian) pair reads (warp box test and alpha) fill the first three
+// 16-byte words.
 //   [0..3]  projected centre split as integer part + remainder (x_hi, y_hi,
 //           x_lo, y_lo); m = hi + lo, hi an integer-valued float, |lo| <= 0.5
-//   [4]     opacity     [5] k (gradient factor)   [6..8] RGB
-//   [9..11] conic (A, B, C) of the inverse 2D covariance (high words)
+//   [4..6]  conic (A, B, C) of the inverse 2D covariance (high words)
+//   [7]     opacity
+//   [8..9]  half-extents (x, y) of the box holding every pixel where alpha
+//           can reach alpha_min (with margin): a warp whose 8x4 pixel block
+//           lies outside skips the Gaussian
+//   [10]    1 when the splat is ill-conditioned (alpha evaluated in
+//           double-float), else 0
+//   [11]    -1 when the camera is inside the 1-sigma ellipsoid (|v_s| <= 1),
+//           else +1
 //   [12..20] M_c = S^-1 R^T R_cw (camera ray -> local scaled), row-major
 //   [21..23] v_s = S^-1 R^T (C - mu)
 //   [24..32] N_w = R S^-1 (scaled-local normal -> world), row-major
 //   [33]    camera-frame z of the centre
 //   [34..36] low words of the conic (double-float A, B, C)
-//   [37]    1 when the splat is ill-conditioned (alpha evaluated in
-//           double-float), else 0
-//   [38..39] half-extents (x, y) of the box holding every pixel where alpha
-//           can reach alpha_min (with margin): a warp whose 8x4 pixel block
-//           lies outside skips the Gaussian
-//   [40..42] kappa_a = z s_a / (s_b s_c): v_s x d_s = kappa (.) M_c (Delta x m~)
+//   [37]    k (gradient factor)
+//   [38..40] RGB
+//   [41..43] kappa_a = z s_a / (s_b s_c): v_s x d_s = kappa (.) M_c (Delta x m~)
 //           (see pair_geometry), the cancellation-free form of the cross
 //           product for Gaussians far from the camera
-//   [43]    -1 when the camera is inside the 1-sigma ellipsoid (|v_s| <= 1),
-//           else +1
 // ----------------------------------------------------------------------------
 enum {
-    R_MXH = 0, R_MYH, R_MXL, R_MYL, R_OP, R_K, R_RGB, R_CON = 9, R_MC = 12,
-    R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34, R_FLAG = 37, R_EXTX = 38, R_EXTY = 39,
-    R_KAP = 40, R_SR = 43, REC_FLOATS = 44
+    R_MXH = 0, R_MYH, R_MXL, R_MYL, R_CON = 4, R_OP = 7, R_EXTX = 8, R_EXTY = 9,
+    R_FLAG = 10, R_SR = 11, R_MC = 12, R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34,
+    R_K = 37, R_RGB = 38, R_KAP = 41, REC_FLOATS = 44
 };
 
 // Pixel of thread tid inside its 16x16 tile: warp w covers the 8x4 block at
