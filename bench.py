@@ -104,12 +104,12 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one render_bwd launch on this workload, from a
-# one-pass ncu capture of the full run (dram__bytes_read.sum 6.837 GB +
-# dram__bytes_write.sum 0.834 GB), valid only for the kernel sources whose
+# one-pass ncu capture of the full run (dram__bytes_read.sum 6.796 GB +
+# dram__bytes_write.sum 0.819 GB), valid only for the kernel sources whose
 # digest is recorded here; any change to them reports null until re-captured.
-BWD_TRAFFIC_BYTES = 7_670_697_984
+BWD_TRAFFIC_BYTES = 7_614_601_216
 BWD_TRAFFIC_SOURCES = ("render_bwd.cu", "splat.cuh", "unigs_internal.cuh", "ff.cuh", "sh.cuh")
-BWD_TRAFFIC_DIGEST = "df9908688e4752c513c61016113d4112c6891be43ea1664be09e3907e10348f2"
+BWD_TRAFFIC_DIGEST = "d83a702a711e90e3ad0100587a3569b9a8c071413eedf5056afb082e81e56e51"
 
 
 def bwd_traffic():
