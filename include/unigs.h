@@ -217,11 +217,11 @@ unigs_status unigs_bin_sort(const unigs_plan* plan, void* ws, int64_t* n_instanc
  * from SH): persistent CTAs pull 16x16 tiles longest list first, Gaussian
  * batches staged in shared memory by bulk (TMA) copies, per-pixel
  * accumulators in registers, early exit when every pixel of the tile has
- * T < T_min.  With bfloat16 features and 9..64 logits (and without
- * UNIGS_FLAG_SIMT_LOGITS) the logit blend of Eq. semantic_render runs on the
- * tensor cores as a per-batch product W F (weights split into two bfloat16
- * parts, float32 accumulation in tensor memory); the other channels do not
- * change.  Non-finite logits are outside the contract (on the tensor-core
+ * T < T_min.  With 9..64 logits (and without UNIGS_FLAG_SIMT_LOGITS) the
+ * logit blend of Eq. semantic_render runs on the tensor cores as a per-batch
+ * product W F (weights split into two bfloat16 parts, float32 features into
+ * two more, float32 accumulation in tensor memory); the other channels do
+ * not change.  Non-finite logits are outside the contract (on the tensor-core
  * path they reach every pixel of the tile batch). */
 unigs_status unigs_render_fwd(const unigs_plan* plan, const unigs_gaussians* g, void* ws,
                               const unigs_outputs* out, unigs_stream stream);

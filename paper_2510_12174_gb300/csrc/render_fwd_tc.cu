@@ -29,6 +29,8 @@
 #include "splat.cuh"
 #include "tcgen05.cuh"
 
+#include <type_traits>
+
 namespace unigs {
 
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
@@ -40,7 +42,7 @@ struct FwdTcParams {
     int64_t n;
     int64_t n_tiles;
     const float* rec;
-    const __nv_bfloat16* sem;  // bfloat16 rows [n][n_sem]
+    const void* sem;           // rows [n][n_sem]: bfloat16, or float32 (F32 kernels)
     const uint32_t* vals;
     const uint2* ranges;
     const uint32_t* order;
@@ -52,15 +54,17 @@ struct FwdTcParams {
     int sem_bulk;
 };
 
-template <int NS, int B>
+template <int NS, int B, bool F32>
 struct FwdTcSmem {
+    using SemT = typename std::conditional<F32, float, __nv_bfloat16>::type;
+    static constexpr int SPLITS_F = F32 ? 2 : 1;  // float32 features: bfloat16 hi + lo
     static constexpr int SBO = 16 * B;            // bytes between 8-row core-matrix groups
     static constexpr int W_BYTES = 128 * B * 2;   // one split of one M-tile
     static constexpr int F_BYTES = NS * B * 2;
-    __align__(128) unsigned char wa[2][2][2][W_BYTES];  // [buffer][split][M-tile]
-    __align__(128) unsigned char fb[2][F_BYTES];        // [buffer] F^T, NS rows x B (K)
+    __align__(128) unsigned char wa[2][2][2][W_BYTES];       // [buffer][split][M-tile]
+    __align__(128) unsigned char fb[2][SPLITS_F][F_BYTES];   // [buffer][split] F^T, NS x B
     __align__(16) float rec[2][B][REC_FLOATS];
-    __align__(16) __nv_bfloat16 semb[2][B][NS];
+    __align__(16) SemT semb[2][B][NS];
     uint64_t bar[2];
     uint64_t mma_bar[2];  // MMA completion per operand buffer
     uint32_t tmem_base;
@@ -72,12 +76,13 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
     return 2 * NS < 32 ? 32u : (uint32_t)(2 * NS);
 }
 
-template <int NS, int B>
-__device__ __forceinline__ void tc_issue_batch(const FwdTcParams& P, FwdTcSmem<NS, B>& S,
+template <int NS, int B, bool F32>
+__device__ __forceinline__ void tc_issue_batch(const FwdTcParams& P, FwdTcSmem<NS, B, F32>& S,
                                                int buf, uint32_t first, int count, int cam) {
+    using SemT = typename FwdTcSmem<NS, B, F32>::SemT;
     // executed by warp 0 only
     const int lane = threadIdx.x & 31;
-    const uint32_t row_bytes = (uint32_t)(P.n_sem * 2);
+    const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(SemT));
     const uint32_t per = REC_FLOATS * 4 + (P.sem_bulk ? row_bytes : 0u);
     if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], per * (uint32_t)count);
     __syncwarp();
@@ -85,7 +90,7 @@ __device__ __forceinline__ void tc_issue_batch(const FwdTcParams& P, FwdTcSmem<N
         const uint32_t g = P.vals[first + i];
         const size_t r = (size_t)cam * (size_t)P.n + g;
         bulk_g2s(&S.rec[buf][i][0], P.rec + r * REC_FLOATS, REC_FLOATS * 4, &S.bar[buf]);
-        const __nv_bfloat16* src = P.sem + (size_t)g * P.n_sem;
+        const SemT* src = static_cast<const SemT*>(P.sem) + (size_t)g * P.n_sem;
         if (P.sem_bulk)
             bulk_g2s(&S.semb[buf][i][0], src, row_bytes, &S.bar[buf]);
         else
@@ -93,11 +98,11 @@ __device__ __forceinline__ void tc_issue_batch(const FwdTcParams& P, FwdTcSmem<N
     }
 }
 
-template <int NS, int B>
+template <int NS, int B, bool F32>
 // batch 16: 45 KB of shared memory and <= 64 registers, 4 CTAs per SM (4 x
 // 128 accumulator columns fill the tensor memory); larger batches: 2
 __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(const FwdTcParams P) {
-    using Sm = FwdTcSmem<NS, B>;
+    using Sm = FwdTcSmem<NS, B, F32>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm& S = *reinterpret_cast<Sm*>(smem_raw);
     const int tid = threadIdx.x;
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
     // once per CTA: zero the staging (rows shorter than NS stay zero-padded),
     // init barriers, allocate the accumulator columns
     for (int j = tid; j < 2 * B * NS; j += 256)
-        (&S.semb[0][0][0])[j] = __float2bfloat16_rn(0.f);
+        (&S.semb[0][0][0])[j] = typename Sm::SemT(0.f);
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
         const int n_items = (int)(range.y - range.x);
         const int n_batches = (n_items + B - 1) / B;
         if (warp == 0 && n_batches > 0)
-            tc_issue_batch<NS, B>(P, S, 0, range.x, min(B, n_items), cam_idx);
+            tc_issue_batch<NS, B, F32>(P, S, 0, range.x, min(B, n_items), cam_idx);
         __syncthreads();
 
         float T = 1.f;
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
         for (int b = 0; b < n_batches; ++b) {
             const int buf = b & 1;
             if (warp == 0 && b + 1 < n_batches)
-                tc_issue_batch<NS, B>(P, S, buf ^ 1, range.x + (b + 1) * B,
+                tc_issue_batch<NS, B, F32>(P, S, buf ^ 1, range.x + (b + 1) * B,
                                       min(B, n_items - (b + 1) * B), cam_idx);
             if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, TC_WAIT_LIMIT)) timed_out = true;
             ++loads[buf];
@@ -190,16 +195,41 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
             }
             const int count = min(B, n_items - b * B);
             // F^T: channel c, Gaussians 8 jc .. 8 jc + 7 as one 16-byte core row
+            // (float32 features: the bfloat16 hi part and the bfloat16 rounding
+            // of the remainder, f = hi + lo + r with |r| <= 2^-18 |f|)
             for (int task = tid; task < NS * (B / 8); task += 256) {
                 const int c = task / (B / 8), jc = task % (B / 8);
-                const unsigned short* col =
-                    reinterpret_cast<const unsigned short*>(&S.semb[buf][0][0]) + c;
-                uint4 q;
-                q.x = (uint32_t)col[(8 * jc + 0) * NS] | ((uint32_t)col[(8 * jc + 1) * NS] << 16);
-                q.y = (uint32_t)col[(8 * jc + 2) * NS] | ((uint32_t)col[(8 * jc + 3) * NS] << 16);
-                q.z = (uint32_t)col[(8 * jc + 4) * NS] | ((uint32_t)col[(8 * jc + 5) * NS] << 16);
-                q.w = (uint32_t)col[(8 * jc + 6) * NS] | ((uint32_t)col[(8 * jc + 7) * NS] << 16);
-                *reinterpret_cast<uint4*>(&S.fb[ob][0] + (c >> 3) * Sm::SBO + jc * 128 + (c & 7) * 16) = q;
+                const int off = (c >> 3) * Sm::SBO + jc * 128 + (c & 7) * 16;
+                if (F32) {
+                    const float* col = reinterpret_cast<const float*>(&S.semb[buf][0][0]) + c;
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float f0 = col[(8 * jc + 2 * e) * NS];
+                        const float f1 = col[(8 * jc + 2 * e + 1) * NS];
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(f0);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(f1);
+                        h[e] = (uint32_t)__bfloat16_as_ushort(h0) |
+                               ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        l[e] = (uint32_t)__bfloat16_as_ushort(
+                                   __float2bfloat16_rn(f0 - __bfloat162float(h0))) |
+                               ((uint32_t)__bfloat16_as_ushort(
+                                    __float2bfloat16_rn(f1 - __bfloat162float(h1)))
+                                << 16);
+                    }
+                    *reinterpret_cast<uint4*>(&S.fb[ob][0][0] + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(&S.fb[ob][F32 ? 1 : 0][0] + off) =
+                        make_uint4(l[0], l[1], l[2], l[3]);
+                } else {
+                    const unsigned short* col =
+                        reinterpret_cast<const unsigned short*>(&S.semb[buf][0][0]) + c;
+                    uint4 q;
+                    q.x = (uint32_t)col[(8 * jc + 0) * NS] | ((uint32_t)col[(8 * jc + 1) * NS] << 16);
+                    q.y = (uint32_t)col[(8 * jc + 2) * NS] | ((uint32_t)col[(8 * jc + 3) * NS] << 16);
+                    q.z = (uint32_t)col[(8 * jc + 4) * NS] | ((uint32_t)col[(8 * jc + 5) * NS] << 16);
+                    q.w = (uint32_t)col[(8 * jc + 6) * NS] | ((uint32_t)col[(8 * jc + 7) * NS] << 16);
+                    *reinterpret_cast<uint4*>(&S.fb[ob][0][0] + off) = q;
+                }
             }
             const bool skip = __all_sync(0xffffffffu, done || timed_out);
             // this thread's W rows: zero, then the weights of the Gaussians it
@@ -252,23 +282,27 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
             }
             fence_async_shared();
             const int alive = __syncthreads_count(!done && !timed_out);
-            // one thread issues the batch's MMAs: 2 splits x 2 M-tiles x B/16 K-steps
+            // one thread issues the batch's MMAs: per M-tile and K-step, W_hi F_hi
+            // and W_lo F_hi, plus W_hi F_lo for float32 features (W_lo F_lo is
+            // below the float32 rounding of the sum)
             if (tid == 0) {
                 tc_fence_after_sync();
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     const uint32_t d = tmem + (uint32_t)(m * NS);
 #pragma unroll
-                    for (int sp = 0; sp < 2; ++sp)
+                    for (int pr = 0; pr < (F32 ? 3 : 2); ++pr) {
+                        const int sw = pr == 1 ? 1 : 0, sf = pr == 2 ? 1 : 0;
 #pragma unroll
                         for (int s = 0; s < B / 16; ++s) {
-                            const uint64_t a = smem_desc_kmajor(&S.wa[ob][sp][m][0] + s * 256,
+                            const uint64_t a = smem_desc_kmajor(&S.wa[ob][sw][m][0] + s * 256,
                                                                 128, Sm::SBO);
                             const uint64_t f =
-                                smem_desc_kmajor(&S.fb[ob][0] + s * 256, 128, Sm::SBO);
-                            const uint32_t acc = (batches_done > 0 || sp > 0 || s > 0) ? 1u : 0u;
+                                smem_desc_kmajor(&S.fb[ob][sf][0] + s * 256, 128, Sm::SBO);
+                            const uint32_t acc = (batches_done > 0 || pr > 0 || s > 0) ? 1u : 0u;
                             mma_bf16(d, a, f, IDESC, acc);
                         }
+                    }
                 }
                 mma_commit(&S.mma_bar[ob]);
             }
@@ -351,30 +385,39 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
     }
 }
 
-template <int NS, int B>
+template <int NS, int B, bool F32>
 static void launch_fwd_tc_t(const FwdTcParams& P, int grid, cudaStream_t st) {
-    const size_t smem = sizeof(FwdTcSmem<NS, B>);
+    const size_t smem = sizeof(FwdTcSmem<NS, B, F32>);
     static bool attr_set = false;  // host-side, set once per instantiation
     if (!attr_set) {
-        cudaFuncSetAttribute(render_fwd_tc_kernel<NS, B>,
+        cudaFuncSetAttribute(render_fwd_tc_kernel<NS, B, F32>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    render_fwd_tc_kernel<NS, B><<<grid, 256, smem, st>>>(P);
+    render_fwd_tc_kernel<NS, B, F32><<<grid, 256, smem, st>>>(P);
 }
 
-template <int B>
+template <int B, bool F32>
 static void launch_fwd_tc_b(const FwdTcParams& P, int grid, cudaStream_t st) {
     if (P.n_sem <= 16)
-        launch_fwd_tc_t<16, B>(P, grid, st);
+        launch_fwd_tc_t<16, B, F32>(P, grid, st);
     else if (P.n_sem <= 32)
-        launch_fwd_tc_t<32, B>(P, grid, st);
+        launch_fwd_tc_t<32, B, F32>(P, grid, st);
     else
-        launch_fwd_tc_t<64, B>(P, grid, st);
+        launch_fwd_tc_t<64, B, F32>(P, grid, st);
+}
+
+template <bool F32>
+static void launch_fwd_tc_f(const FwdTcParams& P, int batch, int grid, cudaStream_t st) {
+    switch (batch) {
+        case 16: launch_fwd_tc_b<16, F32>(P, grid, st); break;
+        case 64: launch_fwd_tc_b<64, F32>(P, grid, st); break;
+        default: launch_fwd_tc_b<32, F32>(P, grid, st); break;
+    }
 }
 
 bool fwd_tc_eligible(const unigs_plan& p, const unigs_gaussians& g) {
-    return p.feat_dtype == 1 && p.n_sem >= 9 && p.n_sem <= UNIGS_MAX_SEM && g.sem != nullptr &&
+    return p.n_sem >= 9 && p.n_sem <= UNIGS_MAX_SEM && g.sem != nullptr &&
            !(p.cfg.flags & UNIGS_FLAG_SIMT_LOGITS);
 }
 
@@ -388,7 +431,7 @@ int launch_render_fwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws
     P.n = p.n;
     P.n_tiles = p.n_tiles;
     P.rec = ws_ptr<float>(ws, p, OFF_REC);
-    P.sem = static_cast<const __nv_bfloat16*>(g.sem);
+    P.sem = g.sem;
     P.vals = sorted_buffer(p) ? ws_ptr<uint32_t>(ws, p, OFF_VALS1) : ws_ptr<uint32_t>(ws, p, OFF_VALS0);
     P.ranges = ws_ptr<uint2>(ws, p, OFF_RANGES);
     P.order = ws_ptr<uint32_t>(ws, p, OFF_ORDER);
@@ -400,7 +443,8 @@ int launch_render_fwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws
     P.alpha_max = p.cfg.alpha_max;
     P.T_min = p.cfg.T_min;
     P.center_depth = (p.cfg.flags & UNIGS_FLAG_CENTER_DEPTH) ? 1 : 0;
-    P.sem_bulk = ((p.n_sem * 2) % 16 == 0) && ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
+    const int esz = p.feat_dtype ? 2 : 4;
+    P.sem_bulk = ((p.n_sem * esz) % 16 == 0) && ((reinterpret_cast<uintptr_t>(P.sem) & 15) == 0);
     cudaMemsetAsync(P.work, 0, sizeof(uint32_t), st);
     // defaults: batch 16, 4 CTAs per SM; at most 4 CTAs per SM hold
     // accumulator columns at once (512 per SM)
@@ -409,11 +453,10 @@ int launch_render_fwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws
     if (ctas > 4) ctas = 4;
     int64_t grid = (int64_t)sm_count() * ctas;
     if (grid > p.n_tiles) grid = p.n_tiles;
-    switch (batch) {
-        case 16: launch_fwd_tc_b<16>(P, (int)grid, st); break;
-        case 64: launch_fwd_tc_b<64>(P, (int)grid, st); break;
-        default: launch_fwd_tc_b<32>(P, (int)grid, st); break;
-    }
+    if (p.feat_dtype)
+        launch_fwd_tc_f<false>(P, batch, (int)grid, st);
+    else
+        launch_fwd_tc_f<true>(P, batch, (int)grid, st);
     return 1;
 }
 

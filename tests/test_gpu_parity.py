@@ -82,15 +82,17 @@ def test_forward_parity_bf16_features():
     assert e["depth"] < TOL_REL and e["logits"] < TOL_REL
 
 
-@pytest.mark.parametrize("n_sem", [12, 32, 64])
-def test_tensor_core_logit_blend(n_sem):
-    """BF16 logits take the tensor-core blend (W F per tile batch, weights in
-    two bfloat16 parts): logits against the oracle at the forward tolerance and
-    against the FP32-pipe blend (UNIGS_FLAG_SIMT_LOGITS) within the split's
-    bound, |dO| <= 2^-18 sum_j w_j |f_j| plus float32 summation order, taken as
-    1e-5 max|f| (sum_j w_j <= 1); every other output is bit-identical."""
+@pytest.mark.parametrize("n_sem,bf16", [(12, True), (32, True), (64, True), (16, False),
+                                        (64, False)])
+def test_tensor_core_logit_blend(n_sem, bf16):
+    """9..64 logits take the tensor-core blend (W F per tile batch, weights in
+    two bfloat16 parts, float32 features in two more): logits against the
+    oracle at the forward tolerance and against the FP32-pipe blend
+    (UNIGS_FLAG_SIMT_LOGITS) within the splits' bound, |dO| <= 2^-18 sum_j w_j
+    |f_j| per split plus float32 summation order, taken as 1e-5 max|f|
+    (sum_j w_j <= 1); every other output is bit-identical."""
     sc, cams = scenes.small_room(n=6000, width=70, height=50, n_sem=n_sem, seed=18,
-                                 feat_bf16=True, n_cams=2)
+                                 feat_bf16=bf16, n_cams=2)
     r_tc, o_tc = _render(sc, cams)
     cfg = abi.unigs_config_default()
     cfg.flags |= abi.UNIGS_FLAG_SIMT_LOGITS
@@ -431,8 +433,11 @@ def test_launch_shape_invariance(batch, ctas):
     tolerance of the oracle (only the order of the float32 atomic additions
     moves)."""
     sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=16, seed=27, n_cams=2)
-    r0, o0 = _render(sc, cams)
+    cfg0 = abi.unigs_config_default()
+    cfg0.flags |= abi.UNIGS_FLAG_SIMT_LOGITS
+    r0, o0 = _render(sc, cams, cfg=cfg0)
     cfg = abi.unigs_config_default()
+    cfg.flags |= abi.UNIGS_FLAG_SIMT_LOGITS
     cfg.batch, cfg.ctas_per_sm = batch, ctas
     cfg.batch_fwd, cfg.ctas_per_sm_fwd = (batch if batch >= 16 else 16), ctas
     r1, o1 = _render(sc, cams, cfg=cfg)
@@ -448,6 +453,23 @@ def test_launch_shape_invariance(batch, ctas):
     torch.cuda.synchronize()
     assert r1.status()[0] == 0
     check_grad_errors(grad_errors(grads, gref))
+
+
+@pytest.mark.parametrize("batch,ctas", [(16, 4), (32, 2), (64, 1)])
+def test_tensor_core_launch_shapes(batch, ctas):
+    """On the tensor-core path the launch shape moves the logits by float32
+    summation order only (the MMA K-steps follow the batches); every other
+    output stays bit-identical."""
+    sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=32, seed=27, n_cams=2,
+                                 feat_bf16=True)
+    r0, o0 = _render(sc, cams)
+    cfg = abi.unigs_config_default()
+    cfg.batch_fwd, cfg.ctas_per_sm_fwd = batch, ctas
+    r1, o1 = _render(sc, cams, cfg=cfg)
+    for k in ("rgb", "depth", "normal_g", "kmap", "T_final", "n_contrib"):
+        assert torch.equal(o0[k], o1[k]), k
+    fmax = float(np.abs(sc.sem).max())
+    assert float((o0["logits"] - o1["logits"]).abs().max()) < 1e-5 * fmax
 
 
 def test_invalid_launch_shape_rejected():
