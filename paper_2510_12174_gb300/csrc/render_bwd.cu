@@ -188,6 +188,9 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
             if (P.go.kmap) g_K = P.go.kmap[pix + idx];
         }
         if (last) atomicMax(&S.max_last, last);
+        // the warp's own last list position: Gaussians behind it are skipped
+        // by the whole warp
+        const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
         __syncthreads();
         const int n_items = (int)S.max_last;
         const int n_batches = (n_items + B - 1) / B;
@@ -209,8 +212,8 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
             if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, BWAIT_LIMIT)) timed_out = true;
             ++loads[buf];
             const int count = min(B, n_items - b * B);
-            if (!__all_sync(0xffffffffu, timed_out)) {
-            for (int j = count - 1; j >= 0; --j) {
+            if (!__all_sync(0xffffffffu, timed_out) && (uint32_t)(b * B) < wlast) {
+            for (int j = min(count, (int)(wlast - (uint32_t)(b * B))) - 1; j >= 0; --j) {
                 const uint32_t pos = (uint32_t)(b * B + j);
                 const float* rc = &S.rec[buf][j][0];
                 if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
