@@ -260,3 +260,36 @@ def unigs_sort_pairs_static(keys_in, vals_in, n, key_bits, keys_out, vals_out, s
 
 def unigs_launches_per_step(plan) -> int:
     return lib().unigs_launches_per_step(ctypes.byref(plan))
+
+
+# include/unigs_train.h ---------------------------------------------------------
+def unigs_loss_lambda_default() -> unigs_loss_lambda:
+    lam = unigs_loss_lambda()
+    lib().unigs_loss_lambda_default(ctypes.byref(lam))
+    return lam
+
+
+def unigs_loss(plan, out, normal_d, tgt, lam, ws, record, grads, stream) -> int:
+    """Combined loss of Sec. 3.4 and its gradients (see include/unigs_train.h)."""
+    return lib().unigs_loss(ctypes.byref(plan), ctypes.byref(out), normal_d, ctypes.byref(tgt),
+                            ctypes.byref(lam), ws, record, ctypes.byref(grads), stream)
+
+
+def unigs_adam_step(groups, n_groups, hp, step, stream) -> int:
+    return lib().unigs_adam_step(groups, n_groups, ctypes.byref(hp), step, stream)
+
+
+def unigs_param_copies(groups, n_groups, stream) -> int:
+    return lib().unigs_param_copies(groups, n_groups, stream)
+
+
+def unigs_prune_workspace_bytes(n) -> int:
+    return lib().unigs_prune_workspace_bytes(n)
+
+
+def unigs_prune_mark(k, n, T_k, ws, n_keep, stream) -> int:
+    return lib().unigs_prune_mark(k, n, T_k, ws, ctypes.byref(n_keep), stream)
+
+
+def unigs_prune_compact(arrays, n_arrays, n, n_keep, ws, stream) -> int:
+    return lib().unigs_prune_compact(arrays, n_arrays, n, n_keep, ws, stream)

@@ -206,3 +206,31 @@ def config_for(scene, cams, base: Optional[abi.unigs_config] = None,
     f, b = hit.get("fwd", {}), hit.get("bwd", {})
     return make_config(b.get("batch", 0), b.get("ctas_per_sm", 0), base,
                        f.get("batch", 0), f.get("ctas_per_sm", 0))
+
+
+def main(argv=None):
+    """Tunes the launch shapes of the synthetic-room workload of the benchmark
+    (or a smaller one) and prints the measured candidates as JSON."""
+    import argparse
+
+    from . import scenes
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--gaussians", type=int, default=1_000_000)
+    ap.add_argument("--views", type=int, default=16)
+    ap.add_argument("--fp32", action="store_true", help="float32 feature storage")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cache", default=None, help="cache file (default: the user cache)")
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    sc, cams = scenes.config3_orbit(args.views, n=args.gaussians, feat_bf16=not args.fp32)
+    ds = rz.DeviceScene.from_scene(sc)
+    path = args.cache or default_cache_path()
+    best = tune(ds, cams, reps=args.reps, cache_path=path, force=True)
+    entry = _load(path).get(workload_key(ds, cams), {})
+    print(json.dumps({"workload": workload_key(ds, cams), "best": best,
+                      "fwd_ms": entry.get("fwd", {}).get("ms"),
+                      "bwd_ms": entry.get("bwd", {}).get("ms")}, indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -252,12 +252,10 @@ class Renderer:
             x = lgrads.get(k)
             setattr(g, k, _ptr(x) if x is not None and x.numel() else None)
         if lam is None:
-            lam = abi.unigs_loss_lambda()
-            abi.lib().unigs_loss_lambda_default(ctypes.byref(lam))
-        abi.check(abi.lib().unigs_loss(ctypes.byref(self.plan), ctypes.byref(self._out_struct(out)),
-                                       _ptr(out["normal_d"]), ctypes.byref(t), ctypes.byref(lam),
-                                       self.ws.data_ptr(), record.data_ptr(), ctypes.byref(g),
-                                       self._stream()), "unigs_loss")
+            lam = abi.unigs_loss_lambda_default()
+        abi.check(abi.unigs_loss(self.plan, self._out_struct(out), _ptr(out["normal_d"]), t, lam,
+                                 self.ws.data_ptr(), record.data_ptr(), g, self._stream()),
+                  "unigs_loss")
         return record
 
     # ----------------------------------------------------------------- misc

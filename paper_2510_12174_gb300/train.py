@@ -80,8 +80,7 @@ class Trainer:
         self.render_cfg = render_cfg
         self.record = torch.zeros(abi.UNIGS_LOSS_RECORD_FLOATS, dtype=torch.float32,
                                   device=self.device)
-        lam = abi.unigs_loss_lambda()
-        abi.lib().unigs_loss_lambda_default(ctypes.byref(lam))
+        lam = abi.unigs_loss_lambda_default()
         for k, val in (self.cfg.lam or {}).items():
             setattr(lam, k, float(val))
         self.lam = lam
@@ -144,7 +143,7 @@ class Trainer:
 
     def _copies(self):
         st = torch.cuda.current_stream(self.device).cuda_stream
-        abi.check(abi.lib().unigs_param_copies(self._groups(False), len(PARAMS), st),
+        abi.check(abi.unigs_param_copies(self._groups(False), len(PARAMS), st),
                   "unigs_param_copies")
 
     def _act_out(self, name):
@@ -173,8 +172,8 @@ class Trainer:
         return self.grads
 
     def adam(self):
-        abi.check(abi.lib().unigs_adam_step(self._groups(True), len(PARAMS), ctypes.byref(self.hp),
-                                            self.step_dev.data_ptr(), self.renderer._stream()),
+        abi.check(abi.unigs_adam_step(self._groups(True), len(PARAMS), self.hp,
+                                      self.step_dev.data_ptr(), self.renderer._stream()),
                   "unigs_adam_step")
 
     def step(self):
@@ -198,12 +197,11 @@ class Trainer:
         """Removes the Gaussians with |k - 1| > T_k; returns the survivors."""
         n = self.n
         st = self.renderer._stream()
-        ws = torch.empty(max(abi.lib().unigs_prune_workspace_bytes(n), 256), dtype=torch.uint8,
+        ws = torch.empty(max(abi.unigs_prune_workspace_bytes(n), 256), dtype=torch.uint8,
                          device=self.device)
         keep = ctypes.c_int64(0)
-        abi.check(abi.lib().unigs_prune_mark(self.raw["k"].data_ptr(), n,
-                                             float(self.cfg.T_k), ws.data_ptr(),
-                                             ctypes.byref(keep), st), "unigs_prune_mark")
+        abi.check(abi.unigs_prune_mark(self.raw["k"].data_ptr(), n, float(self.cfg.T_k),
+                                       ws.data_ptr(), keep, st), "unigs_prune_mark")
         nk = int(keep.value)
         arrays = []
         new = {}
@@ -232,7 +230,7 @@ class Trainer:
             new[("m", name)] = plan(name, self.m[name], 0.0 if reset else None)
             new[("v", name)] = plan(name, self.v[name], 0.0 if reset else None)
         arr = (abi.unigs_prune_array * len(arrays))(*arrays)
-        abi.check(abi.lib().unigs_prune_compact(arr, len(arrays), n, nk, ws.data_ptr(), st),
+        abi.check(abi.unigs_prune_compact(arr, len(arrays), n, nk, ws.data_ptr(), st),
                   "unigs_prune_compact")
         for name in PARAMS:
             self.raw[name] = new[("raw", name)]
