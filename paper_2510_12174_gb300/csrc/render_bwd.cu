@@ -67,7 +67,8 @@ struct BwdSmem {
     float gO[TILE_PIX * NS];
     float wv[8][32];  // per warp: the weights w of its pixels for the current Gaussian
     uint32_t ids[2][B];
-    uint64_t bar[2];
+    uint64_t bar[2];   // batch staged (bulk bytes + the producer warp's arrival)
+    uint64_t cons[2];  // batch consumed (one arrival per warp)
     uint32_t max_last;
     int tile;
 };
@@ -96,7 +97,7 @@ __device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, B>& S,
     const int lane = threadIdx.x & 31;
     const uint32_t row_bytes = (uint32_t)(P.n_sem * sizeof(float));
     const uint32_t per = REC_FLOATS * 4 + (P.sem_bulk ? row_bytes : 0u);
-    if (lane == 0) mbar_arrive_expect_tx(&S.bar[buf], per * (uint32_t)count);
+    if (lane == 0) mbar_expect_tx(&S.bar[buf], per * (uint32_t)count);
     __syncwarp();
     for (int i = lane; i < count; i += 32) {
         const uint32_t g = P.vals[first + i];
@@ -111,6 +112,10 @@ __device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, B>& S,
                 for (int c = 0; c < P.n_sem; ++c) S.sem[buf][i][c] = src[c];
         }
     }
+    // the warp's plain stores (ids, unaligned rows) are released by the
+    // producer's arrival, which the consumers' wait acquires
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.bar[buf]);
 }
 
 __device__ __forceinline__ void cross_acc(const float* a, const float* b, float* c) {
@@ -131,11 +136,14 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
+        mbar_init(&S.cons[0], 8);
+        mbar_init(&S.cons[1], 8);
         fence_mbar_init();
     }
     for (int j = tid; j < 2 * B * NS; j += 256) (&S.sem[0][0][0])[j] = 0.f;
     __syncthreads();
     uint32_t loads[2] = {0u, 0u};  // completed loads per buffer (uniform)
+    uint32_t used[2] = {0u, 0u};   // completed consumptions per buffer (uniform)
     bool timed_out = false;
 
     for (;;) {
@@ -195,20 +203,24 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         const int n_items = (int)S.max_last;
         const int n_batches = (n_items + B - 1) / B;
         const uint2 range = P.ranges[gtile];
+        // Staging pipeline: warp 0 stages batch it+1 while every warp composites
+        // batch it; a buffer is restaged only after all 8 warps have arrived on
+        // its "consumed" barrier, so the warps never meet at a CTA barrier
+        // inside the tile.
+        auto produce = [&](int bf, uint32_t first, int cnt) {
+            if (used[bf] > 0 &&
+                !mbar_wait_bounded(&S.cons[bf], (used[bf] - 1) & 1u, BWAIT_LIMIT))
+                timed_out = true;
+            bwd_issue<NS, B>(P, S, bf, first, cnt, cam_idx);
+        };
         if (warp == 0 && n_batches > 0)
-            bwd_issue<NS, B>(P, S, 0, range.x + (n_batches - 1) * B,
-                             min(B, n_items - (n_batches - 1) * B), cam_idx);
-        // ids and unaligned semantic rows are staged with plain stores: make
-        // the first batch visible (later batches are ordered by the
-        // end-of-batch barrier)
-        __syncthreads();
+            produce(0, range.x + (n_batches - 1) * B, min(B, n_items - (n_batches - 1) * B));
 
         float Sacc = 0.f;  // sum over already processed (later) Gaussians of w_j G_j
         for (int it = 0; it < n_batches; ++it) {
             const int b = n_batches - 1 - it;
             const int buf = it & 1;
-            if (warp == 0 && b > 0)
-                bwd_issue<NS, B>(P, S, buf ^ 1, range.x + (b - 1) * B, B, cam_idx);
+            if (warp == 0 && b > 0) produce(buf ^ 1, range.x + (b - 1) * B, B);
             if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, BWAIT_LIMIT)) timed_out = true;
             ++loads[buf];
             const int count = min(B, n_items - b * B);
@@ -382,7 +394,10 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 }
             }
             }
-            __syncthreads();
+            // this warp is done with the batch's buffers
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.cons[buf]);
+            ++used[buf];
         }
         // a bounded wait that gave up ends the CTA (uniformly)
         if (__syncthreads_or(timed_out)) break;
