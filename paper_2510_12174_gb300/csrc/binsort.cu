@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256)
             cr[4] = c1.x; cr[5] = c1.y; cr[6] = c1.z; cr[7] = c1.w;
         }
         const int nt = (x1 - x0) * (y1 - y0);
-        if (cnt && nt <= 32) {
+        if (cnt && nt <= COOP_TILES) {
             const uint32_t o_end = o + cnt;
             for (int ty = y0; ty < y1; ++ty)
                 for (int tx = x0; tx < x1; ++tx) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256)
                     ++o;
                 }
         }
-        unsigned big = __ballot_sync(0xffffffffu, cnt && nt > 32);
+        unsigned big = __ballot_sync(0xffffffffu, cnt && nt > COOP_TILES);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;

@@ -245,7 +245,6 @@ __device__ __forceinline__ uint32_t count_kept_serial(const float* cr, int x0, i
     return kept;
 }
 
-constexpr int COOP_TILES = 32;  // rectangles above this are tested by the whole warp
 
 __global__ void __launch_bounds__(256)
     preprocess_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab, int n_cams,

@@ -166,6 +166,10 @@ __device__ __forceinline__ bool tile_keep(const float* __restrict__ cr, int tx, 
 }
 
 constexpr int SORT_ITEMS = 2048;   // keys per sort block (256 threads x 8)
+// Tile rectangles with more tiles than this are culled-tested and emitted by
+// the whole warp (32 tiles per step) rather than by their own thread: a lane
+// with a long serial loop would hold its warp (measured: 4 beats 8, 16, 32).
+constexpr int COOP_TILES = 4;
 constexpr int SCAN_ITEMS = 4096;   // elements per scan block (256 threads x 16)
 constexpr int LOSS_MAX_BLOCKS = 2048;  // block partials of the loss reduction
 
