@@ -2,9 +2,8 @@
 import numpy as np
 import torch
 
-# Forward tolerances: absolute 1e-4 for RGB, the
-# ellipsoid normal, k and T; 1e-4 relative to max(|ref|, RMS of the channel)
-# for depth and logits.
+# Forward tolerances: absolute 1e-4 for RGB, the ellipsoid normal, k and T;
+# 1e-4 relative to max(|ref|, RMS of the channel) for depth and logits.
 TOL_ABS = 1e-4
 TOL_REL = 1e-4
 
