@@ -135,7 +135,9 @@ typedef struct {
  * alpha_min 1/255, alpha_max 0.99, T_min 1e-4, lowpass 0.3 (the 3DGS values
  * the paper keeps, Sec. 3.4), step1 1, step2 2, lambda 0.5 (Alg. 1; the
  * paper does not print its values), and 0 (= the library's choice) for every
- * launch-shape field.  The launch shape changes the speed only: the forward
+ * launch-shape field.  unigs_plan_init rejects settings outside
+ * 0 <= alpha_min <= alpha_max < 1 (the backward divides by 1 - alpha),
+ * 0 <= T_min < 1 and a finite lowpass >= 0.  The launch shape changes the speed only: the forward
  * outputs do not depend on it (the tensor-core logit blend: up to float32
  * summation order), the gradients up to float32 atomic summation order. */
 typedef struct {

@@ -107,6 +107,13 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
         unigs_config_default(&plan->cfg);
     if (plan->cfg.step1 < 1 || plan->cfg.step1 > 4 || plan->cfg.step2 < 1 || plan->cfg.step2 > 4)
         return UNIGS_ERR_INVALID_ARG;
+    // the backward restores T by dividing by 1 - alpha, alpha <= alpha_max
+    // (comparisons written so that NaN fails them)
+    if (!(plan->cfg.alpha_min >= 0.f && plan->cfg.alpha_min <= plan->cfg.alpha_max &&
+          plan->cfg.alpha_max < 1.f) ||
+        !(plan->cfg.T_min >= 0.f && plan->cfg.T_min < 1.f) ||
+        !(plan->cfg.lowpass >= 0.f && plan->cfg.lowpass < 1e30f))
+        return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.flags & ~(UNIGS_FLAG_CENTER_DEPTH | UNIGS_FLAG_SIMT_LOGITS))
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.batch != 0 && plan->cfg.batch != 8 && plan->cfg.batch != 16 &&

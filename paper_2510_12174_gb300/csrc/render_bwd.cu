@@ -65,7 +65,7 @@ struct BwdSmem {
     float rec[2][B][REC_FLOATS];
     float sem[2][B][NS];
     float gO[TILE_PIX * NS];
-    float wv[8][32];  // per warp: the weights w of its pixels for the current Gaussian
+    float2 wv[8][32];  // per warp: (w, w) of its pixels for the current Gaussian
     uint32_t ids[2][B];
     uint64_t bar[2];   // batch staged (bulk bytes + the producer warp's arrival)
     uint64_t cons[2];  // batch consumed (one arrival per warp)
@@ -79,17 +79,19 @@ __device__ __forceinline__ int go_index(int p, int c) {
     return p * NS + ((((c >> 2) ^ p) & (NS / 4 - 1)) << 2) + (c & 3);
 }
 
-// dot(gO row p, semantic row) with 16-byte shared-memory loads.
+// dot(gO row p, semantic row) with 16-byte shared-memory loads and packed
+// float32 FMAs (four partial sums, one per channel residue mod 4).
 template <int NS>
 __device__ __forceinline__ float sem_dot(const float* go, int p, const float* row) {
-    float acc = 0.f;
+    float2 acc01 = make_float2(0.f, 0.f), acc23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < NS / 4; ++c) {
         const float4 a = *reinterpret_cast<const float4*>(go + go_index<NS>(p, 4 * c));
         const float4 b = reinterpret_cast<const float4*>(row)[c];
-        acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+        acc01 = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), acc01);
+        acc23 = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), acc23);
     }
-    return acc;
+    return (acc01.x + acc23.x) + (acc01.y + acc23.y);
 }
 template <int NS, int B>
 __device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, B>& S, int buf,
@@ -240,7 +242,10 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                     if (alpha >= P.alpha_min) {
                         contrib = true;
                         const float om = 1.f - alpha;
-                        T = T / om;
+                        // om >= 1 - alpha_max: one approximate reciprocal serves
+                        // the transmittance restoration and dL/dalpha
+                        const float rom = __fdividef(1.f, om);
+                        T = T * rom;
                         w = alpha * T;
                         PairGeom G;
                         pair_geometry(rc, xt, yt, dx, dy, ifx, ify, G);
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                                          g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
                                          sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
                                          sem_dot<NS>(S.gO, tid, &S.sem[buf][j][0]);
-                        const float dL_da = T * Gi - Sacc / om;
+                        const float dL_da = T * Gi - Sacc * rom;
                         Sacc = fmaf(w, Gi, Sacc);
                         // alpha = min(alpha_max, op * Gs)
                         const bool clamped = rc[R_OP] * Gs > P.alpha_max;
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                         gv[G_K] = w * g_K;
                         const float* vs = rc + R_VS;
                         const float* Nw = rc + R_NW;
-                        const float inv_a = 1.f / G.a;
+                        const float inv_a = __fdividef(1.f, G.a);
                         float g_ds[3] = {0.f, 0.f, 0.f}, g_vs[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
                         // depth t_mid = -b'/a
                         const float g_t = w * g_D;
@@ -310,7 +315,8 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                                                        g_p[2] * G.ds[2]);
 #pragma unroll
                             for (int i = 0; i < 3; ++i) g_ds[i] -= G.sr * G.h * g_p[i];
-                            g_disc = g_h * 0.5f * inv_a * inv_a / G.h;
+                            // dh/ddisc = 1 / (2 a sqrt(disc))
+                            g_disc = 0.5f * g_h * inv_a * rsqrtf(G.disc);
                             g_a -= g_h * G.h * inv_a;
                         }
                         // disc = a - |cv|^2
@@ -354,29 +360,32 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                             // channels are then added.  Cheaper than looping over the
                             // contributing lanes only: most warps have many.
                             constexpr int LPR = NS / 4, RPS = 32 / LPR;
-                            S.wv[warp][lane] = w;
+                            // w is stored twice so one 8-byte load gives the
+                            // packed FMAs their operand pair
+                            S.wv[warp][lane] = make_float2(w, w);
                             __syncwarp();
                             const int h = lane / LPR, c4 = lane % LPR;
                             const float* rowbase = S.gO + (warp * 32 + h) * NS;
-                            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                            float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
 #pragma unroll
                             for (int i = 0; i < LPR; ++i) {
                                 const int r = i * RPS + h;
-                                const float wr = S.wv[warp][r];
+                                const float2 wr = S.wv[warp][r];
                                 const float4 go = *reinterpret_cast<const float4*>(
                                     rowbase + i * RPS * NS + ((c4 ^ (r & (LPR - 1))) << 2));
-                                acc.x = fmaf(wr, go.x, acc.x);
-                                acc.y = fmaf(wr, go.y, acc.y);
-                                acc.z = fmaf(wr, go.z, acc.z);
-                                acc.w = fmaf(wr, go.w, acc.w);
+                                a01 = __ffma2_rn(wr, make_float2(go.x, go.y), a01);
+                                a23 = __ffma2_rn(wr, make_float2(go.z, go.w), a23);
                             }
 #pragma unroll
                             for (int o = LPR; o < 32; o <<= 1) {
-                                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-                                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-                                acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-                                acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+                                a01 = __fadd2_rn(a01, make_float2(
+                                    __shfl_xor_sync(0xffffffffu, a01.x, o),
+                                    __shfl_xor_sync(0xffffffffu, a01.y, o)));
+                                a23 = __fadd2_rn(a23, make_float2(
+                                    __shfl_xor_sync(0xffffffffu, a23.x, o),
+                                    __shfl_xor_sync(0xffffffffu, a23.y, o)));
                             }
+                            const float4 acc = make_float4(a01.x, a01.y, a23.x, a23.y);
                             __syncwarp();
                             const int c = 4 * c4;
                             if (h == 0 && c < P.n_sem) {

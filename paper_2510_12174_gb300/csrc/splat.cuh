@@ -87,6 +87,14 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 //   v_s x d_s = det(S^-1) S Q (d~ x p_c) = kappa (.) M_c (Delta x m~),
 // Delta = d~ - m~ = ((u - m_x)/fx, (v - m_y)/fy, 0) from the exactly formed
 // pixel offset of the splat, kappa_a = z s_a / (s_b s_c): no cancellation.
+// Square root by the approximate hardware instruction (a few ulp; subnormal
+// inputs supported): the pair geometry feeds tolerance-checked outputs only.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct PairGeom {
     float ds[3], a, bp, t, cv[3], disc, pm[3], h, p[3], m[3], inv_m, sr;
     bool hit, inside;
@@ -103,7 +111,7 @@ __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, floa
     for (int i = 0; i < 3; ++i) G.ds[i] = fmaf(M[3 * i], xt, fmaf(M[3 * i + 1], yt, M[3 * i + 2]));
     G.a = fmaf(G.ds[0], G.ds[0], fmaf(G.ds[1], G.ds[1], G.ds[2] * G.ds[2]));
     G.bp = fmaf(vs[0], G.ds[0], fmaf(vs[1], G.ds[1], vs[2] * G.ds[2]));
-    const float inv_a = 1.f / G.a;
+    const float inv_a = __fdividef(1.f, G.a);  // a = |d_s|^2 > 0, far below 2^126
     G.t = -G.bp * inv_a;
     {
         const float Dx = dxp * ifx, Dy = dyp * ify;
@@ -122,7 +130,7 @@ __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, floa
     G.sr = rc[R_SR];
     G.inside = G.sr < 0.f;
     G.hit = G.disc > 0.f;
-    G.h = G.hit ? sqrtf(G.disc) * inv_a : 0.f;
+    G.h = G.hit ? sqrt_approx(G.disc) * inv_a : 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) G.p[i] = fmaf(-G.sr * G.h, G.ds[i], G.pm[i]);
     const float* N = rc + R_NW;

@@ -265,22 +265,33 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 // ----------------------------------------------------------------------------
 // Warp transpose-reduction: every lane holds v[32]; afterwards lane L holds
-// the warp-wide sum of element L (recursive halving, 31 shuffles).
+// the warp-wide sum of element L (recursive halving, 31 shuffles).  The adds
+// of neighbouring elements are issued as packed float32 pairs; each element
+// still sees the same additions in the same order.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float warp_reduce_transpose32(float (&v)[32], int lane) {
 #pragma unroll
-    for (int step = 0; step < 5; ++step) {
+    for (int step = 0; step < 4; ++step) {
         const int off = 16 >> step;
         const int half = 16 >> step;  // current length is 2*half
         const bool upper = (lane & off) != 0;
 #pragma unroll
-        for (int k = 0; k < half; ++k) {
-            float send = upper ? v[k] : v[k + half];
-            float keep = upper ? v[k + half] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        for (int k = 0; k < half; k += 2) {
+            const float2 lo = make_float2(v[k], v[k + 1]);
+            const float2 hi = make_float2(v[k + half], v[k + half + 1]);
+            const float2 send = upper ? lo : hi;
+            const float2 keep = upper ? hi : lo;
+            const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, off),
+                                            __shfl_xor_sync(0xffffffffu, send.y, off));
+            const float2 sum = __fadd2_rn(keep, recv);
+            v[k] = sum.x;
+            v[k + 1] = sum.y;
         }
     }
-    return v[0];
+    const bool upper = (lane & 1) != 0;
+    const float send = upper ? v[0] : v[1];
+    const float keep = upper ? v[1] : v[0];
+    return keep + __shfl_xor_sync(0xffffffffu, send, 1);
 }
 
 }  // namespace unigs

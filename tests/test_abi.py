@@ -153,7 +153,10 @@ def test_launch_shape_fields_are_validated(lib):
     for field, value, ok in (("batch", 8, True), ("batch", 48, False), ("batch_fwd", 8, False),
                              ("batch_fwd", 64, True), ("ctas_per_sm", 9, False),
                              ("ctas_per_sm_fwd", 4, True), ("flags", 4, False),
-                             ("flags", 3, True)):
+                             ("flags", 3, True), ("alpha_max", 1.0, False),
+                             ("alpha_max", 0.999, True), ("alpha_max", float("nan"), False),
+                             ("alpha_min", -1e-3, False), ("alpha_min", 0.995, False),
+                             ("T_min", 1.0, False), ("lowpass", float("inf"), False)):
         cfg = lib.unigs_config_default()
         setattr(cfg, field, value)
         want = lib.UNIGS_OK if ok else lib.UNIGS_ERR_INVALID_ARG
