@@ -231,122 +231,117 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 const uint32_t pos = (uint32_t)(b * B + j);
                 const float* rc = &S.rec[buf][j][0];
                 if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
+                // alpha of every lane; the warp runs the pair's gradient only if
+                // some lane contributes, and then as a whole: a lane that does not
+                // contribute carries w = 0 and dL/dalpha = 0, which makes every
+                // entry of its gradient vector zero (all intermediates are finite)
+                float dx, dy, Gs;
+                const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                const bool contrib = !timed_out && pos < last && alpha >= P.alpha_min;
+                if (!__any_sync(0xffffffffu, contrib)) continue;
                 float gv[32];
+                const float om = 1.f - alpha;
+                // om >= 1 - alpha_max: one approximate reciprocal serves the
+                // transmittance restoration and dL/dalpha
+                const float rom = __fdividef(1.f, om);
+                if (contrib) T = T * rom;
+                const float w = contrib ? alpha * T : 0.f;
+                PairGeom G;
+                pair_geometry(rc, xt, yt, dx, dy, ifx, ify, G);
+                const float depth = P.center_depth ? rc[R_Z] : G.t;
+                const float sg = G.inside ? -1.f : 1.f;
+                float nh[3];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) gv[k] = 0.f;
-                float w = 0.f;
-                bool contrib = false;
-                if (!timed_out && pos < last) {
-                    float dx, dy, Gs;
-                    const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
-                    if (alpha >= P.alpha_min) {
-                        contrib = true;
-                        const float om = 1.f - alpha;
-                        // om >= 1 - alpha_max: one approximate reciprocal serves
-                        // the transmittance restoration and dL/dalpha
-                        const float rom = __fdividef(1.f, om);
-                        T = T * rom;
-                        w = alpha * T;
-                        PairGeom G;
-                        pair_geometry(rc, xt, yt, dx, dy, ifx, ify, G);
-                        const float depth = P.center_depth ? rc[R_Z] : G.t;
-                        const float sg = G.inside ? -1.f : 1.f;
-                        float nh[3];
+                for (int i = 0; i < 3; ++i) nh[i] = G.m[i] * G.inv_m;
+                // G_i: upstream gradient . features of Gaussian i
+                const float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
+                                 g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
+                                 sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
+                                 sem_dot<NS>(S.gO, tid, &S.sem[buf][j][0]);
+                const float dL_da = contrib ? T * Gi - Sacc * rom : 0.f;
+                Sacc = fmaf(w, Gi, Sacc);
+                // alpha = min(alpha_max, op * Gs)
+                const bool clamped = rc[R_OP] * Gs > P.alpha_max;
+                const float g_pow = clamped ? 0.f : dL_da * alpha;
+                gv[G_OP] = clamped ? 0.f : dL_da * Gs;
+                // power = -1/2 D^T K D: dL/dm = g u, dL/dcov = g/2 u u^T, u = K D
+                float kux, kuy;
+                splat_kdelta(rc, uf, vf, dx, dy, &kux, &kuy);
+                gv[G_CA] = 0.5f * g_pow * kux * kux;
+                gv[G_CB] = g_pow * kux * kuy;
+                gv[G_CC] = 0.5f * g_pow * kuy * kuy;
+                gv[G_MX] = kux * g_pow;
+                gv[G_MY] = kuy * g_pow;
+                gv[G_RGB] = w * g_rgb[0];
+                gv[G_RGB + 1] = w * g_rgb[1];
+                gv[G_RGB + 2] = w * g_rgb[2];
+                gv[G_K] = w * g_K;
+                const float* vs = rc + R_VS;
+                const float* Nw = rc + R_NW;
+                const float inv_a = __fdividef(1.f, G.a);
+                float g_ds[3] = {0.f, 0.f, 0.f}, g_vs[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
+                // depth t_mid = -b'/a
+                const float g_t = w * g_D;
+                gv[G_Z] = P.center_depth ? g_t : 0.f;
+                if (!P.center_depth) {
+                    const float g_bp = -g_t * inv_a;
+                    g_a -= g_t * G.t * inv_a;
 #pragma unroll
-                        for (int i = 0; i < 3; ++i) nh[i] = G.m[i] * G.inv_m;
-                        // G_i: upstream gradient . features of Gaussian i
-                        const float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
-                                         g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
-                                         sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
-                                         sem_dot<NS>(S.gO, tid, &S.sem[buf][j][0]);
-                        const float dL_da = T * Gi - Sacc * rom;
-                        Sacc = fmaf(w, Gi, Sacc);
-                        // alpha = min(alpha_max, op * Gs)
-                        const bool clamped = rc[R_OP] * Gs > P.alpha_max;
-                        const float g_pow = clamped ? 0.f : dL_da * alpha;
-                        gv[G_OP] = clamped ? 0.f : dL_da * Gs;
-                        // power = -1/2 D^T K D: dL/dm = g u, dL/dcov = g/2 u u^T, u = K D
-                        float kux, kuy;
-                        splat_kdelta(rc, uf, vf, dx, dy, &kux, &kuy);
-                        gv[G_CA] = 0.5f * g_pow * kux * kux;
-                        gv[G_CB] = g_pow * kux * kuy;
-                        gv[G_CC] = 0.5f * g_pow * kuy * kuy;
-                        gv[G_MX] = kux * g_pow;
-                        gv[G_MY] = kuy * g_pow;
-                        gv[G_RGB] = w * g_rgb[0];
-                        gv[G_RGB + 1] = w * g_rgb[1];
-                        gv[G_RGB + 2] = w * g_rgb[2];
-                        gv[G_K] = w * g_K;
-                        const float* vs = rc + R_VS;
-                        const float* Nw = rc + R_NW;
-                        const float inv_a = __fdividef(1.f, G.a);
-                        float g_ds[3] = {0.f, 0.f, 0.f}, g_vs[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
-                        // depth t_mid = -b'/a
-                        const float g_t = w * g_D;
-                        if (P.center_depth) {
-                            gv[G_Z] = g_t;
-                        } else {
-                            const float g_bp = -g_t * inv_a;
-                            g_a -= g_t * G.t * inv_a;
-#pragma unroll
-                            for (int i = 0; i < 3; ++i) {
-                                g_vs[i] = g_bp * G.ds[i];
-                                g_ds[i] = g_bp * vs[i];
-                            }
-                        }
-                        // normal n = sg * m / |m|, m = N_w p
-                        const float gn[3] = {w * g_N[0], w * g_N[1], w * g_N[2]};
-                        const float dgn = gn[0] * nh[0] + gn[1] * nh[1] + gn[2] * nh[2];
-                        float g_m[3];
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) g_m[i] = sg * (gn[i] - dgn * nh[i]) * G.inv_m;
-#pragma unroll
-                        for (int r = 0; r < 3; ++r)
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) gv[G_NW + 3 * r + c] = g_m[r] * G.p[c];
-                        float g_p[3];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            g_p[c] = Nw[c] * g_m[0] + Nw[3 + c] * g_m[1] + Nw[6 + c] * g_m[2];
-                        // p = p_mid - sr h d_s, h = sqrt(disc)/a
-                        float g_disc = 0.f;
-                        if (G.hit) {
-                            const float g_h = -G.sr * (g_p[0] * G.ds[0] + g_p[1] * G.ds[1] +
-                                                       g_p[2] * G.ds[2]);
-#pragma unroll
-                            for (int i = 0; i < 3; ++i) g_ds[i] -= G.sr * G.h * g_p[i];
-                            // dh/ddisc = 1 / (2 a sqrt(disc))
-                            g_disc = 0.5f * g_h * inv_a * rsqrtf(G.disc);
-                            g_a -= g_h * G.h * inv_a;
-                        }
-                        // disc = a - |cv|^2
-                        g_a += g_disc;
-                        float g_cv[3];
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) g_cv[i] = -2.f * g_disc * G.cv[i];
-                        // p_mid = (d_s x cv) / a
-                        const float g_q[3] = {g_p[0] * inv_a, g_p[1] * inv_a, g_p[2] * inv_a};
-                        cross_acc(G.cv, g_q, g_ds);
-                        cross_acc(g_q, G.ds, g_cv);
-                        g_a -= (g_p[0] * G.pm[0] + g_p[1] * G.pm[1] + g_p[2] * G.pm[2]) * inv_a;
-                        // cv = v_s x d_s
-                        cross_acc(G.ds, g_cv, g_vs);
-                        cross_acc(g_cv, vs, g_ds);
-                        // a = d_s . d_s
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) g_ds[i] = fmaf(2.f * g_a, G.ds[i], g_ds[i]);
-                        // d_s = M_c d~
-                        const float dt[3] = {xt, yt, 1.f};
-#pragma unroll
-                        for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) gv[G_MC + 3 * r + c] = g_ds[r] * dt[c];
-                            gv[G_VS + r] = g_vs[r];
-                        }
+                    for (int i = 0; i < 3; ++i) {
+                        g_vs[i] = g_bp * G.ds[i];
+                        g_ds[i] = g_bp * vs[i];
                     }
                 }
-                const unsigned cmask = __ballot_sync(0xffffffffu, contrib);
-                if (cmask) {
+                // normal n = sg * m / |m|, m = N_w p
+                const float gn[3] = {w * g_N[0], w * g_N[1], w * g_N[2]};
+                const float dgn = gn[0] * nh[0] + gn[1] * nh[1] + gn[2] * nh[2];
+                float g_m[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g_m[i] = sg * (gn[i] - dgn * nh[i]) * G.inv_m;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) gv[G_NW + 3 * r + c] = g_m[r] * G.p[c];
+                float g_p[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    g_p[c] = Nw[c] * g_m[0] + Nw[3 + c] * g_m[1] + Nw[6 + c] * g_m[2];
+                // p = p_mid - sr h d_s, h = sqrt(disc)/a
+                float g_disc = 0.f;
+                if (G.hit) {
+                    const float g_h = -G.sr * (g_p[0] * G.ds[0] + g_p[1] * G.ds[1] +
+                                               g_p[2] * G.ds[2]);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) g_ds[i] -= G.sr * G.h * g_p[i];
+                    // dh/ddisc = 1 / (2 a sqrt(disc))
+                    g_disc = 0.5f * g_h * inv_a * rsqrtf(G.disc);
+                    g_a -= g_h * G.h * inv_a;
+                }
+                // disc = a - |cv|^2
+                g_a += g_disc;
+                float g_cv[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g_cv[i] = -2.f * g_disc * G.cv[i];
+                // p_mid = (d_s x cv) / a
+                const float g_q[3] = {g_p[0] * inv_a, g_p[1] * inv_a, g_p[2] * inv_a};
+                cross_acc(G.cv, g_q, g_ds);
+                cross_acc(g_q, G.ds, g_cv);
+                g_a -= (g_p[0] * G.pm[0] + g_p[1] * G.pm[1] + g_p[2] * G.pm[2]) * inv_a;
+                // cv = v_s x d_s
+                cross_acc(G.ds, g_cv, g_vs);
+                cross_acc(g_cv, vs, g_ds);
+                // a = d_s . d_s
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g_ds[i] = fmaf(2.f * g_a, G.ds[i], g_ds[i]);
+                // d_s = M_c d~
+                const float dt[3] = {xt, yt, 1.f};
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) gv[G_MC + 3 * r + c] = g_ds[r] * dt[c];
+                    gv[G_VS + r] = g_vs[r];
+                }
+                {
                     const uint32_t g = S.ids[buf][j];
                     const size_t rix = (size_t)cam_idx * (size_t)P.n + g;
                     const float tot = warp_reduce_transpose32(gv, lane);
