@@ -367,9 +367,30 @@ __global__ void __launch_bounds__(256)
             for (int b = 0; b < 3; ++b) o[R_NW + a * 3 + b] = rc.R[a][b] * is[b];
         }
         o[R_Z] = rc.pz;
-        o[R_KAP + 0] = rc.pz * sx / (sy * sz);
-        o[R_KAP + 1] = rc.pz * sy / (sx * sz);
-        o[R_KAP + 2] = rc.pz * sz / (sx * sy);
+        {
+            // v_s x d_s without cancellation (see pair_geometry): with
+            // Q = R^T R_cw, M_c = S^-1 Q and p_c = z m~ (m~ = p_c / z, the
+            // centre's ray), v_s x d_s = det(S^-1) S Q (d~ x p_c)
+            // = kappa (.) M_c (Delta x m~), kappa_a = z s_a / (s_b s_c), where
+            // Delta = d~ - m~ = (dx / fx, dy / fy, 0) for the pixel offset
+            // (dx, dy) from the projected centre.  Delta x m~ = (Dy, -Dx,
+            // Dx m~_y - Dy m~_x) is linear in (dx, dy), so the product is
+            // dx P1 + dy P2 with
+            //   P1_a = kappa_a (M_a2 m~_y - M_a1) / fx,
+            //   P2_a = kappa_a (M_a0 - M_a2 m~_x) / fy.
+            const float iz = 1.f / rc.pz;
+            const float mtx = rc.px * iz, mty = rc.py * iz;
+            const float kap[3] = {rc.pz * sx / (sy * sz), rc.pz * sy / (sx * sz),
+                                  rc.pz * sz / (sx * sy)};
+            const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float* Ma = o + R_MC + 3 * a;
+                o[R_P1 + a] = kap[a] * fmaf(Ma[2], mty, -Ma[1]) * ifx;
+                o[R_P2 + a] = kap[a] * fmaf(-Ma[2], mtx, Ma[0]) * ify;
+            }
+            o[R_PAD] = 0.f;
+        }
         {
             const float* v = o + R_VS;
             const float vv = fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2]));

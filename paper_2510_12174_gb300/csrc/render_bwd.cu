@@ -170,7 +170,6 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         const bool inside = u < cam.width && v < cam.height;
         const float uf = (float)u, vf = (float)v;
         const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
-        const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
         const int W = cam.width;
         const int64_t HW = (int64_t)cam.height * W;
         const int64_t pix = cam.pix_off;
@@ -247,7 +246,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 if (contrib) T = T * rom;
                 const float w = contrib ? alpha * T : 0.f;
                 PairGeom G;
-                pair_geometry(rc, xt, yt, dx, dy, ifx, ify, G);
+                pair_geometry(rc, xt, yt, dx, dy, G);
                 const float depth = P.center_depth ? rc[R_Z] : G.t;
                 const float sg = G.inside ? -1.f : 1.f;
                 float nh[3];

@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
         const bool inside = u < cam.width && v < cam.height;
         const float uf = (float)u, vf = (float)v;
         const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;
-        const float ifx = 1.f / cam.fx, ify = 1.f / cam.fy;
 
         const uint2 range = P.ranges[gtile];
         const int n_items = (int)(range.y - range.x);
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
                     ++n_blend;
                     const float w = alpha * T;
                     PairGeom G;
-                    pair_geometry(rc, xt, yt, dx, dy, ifx, ify, G);
+                    pair_geometry(rc, xt, yt, dx, dy, G);
                     const float depth = P.center_depth ? rc[R_Z] : G.t;
                     const float nsg = (G.inside ? -G.inv_m : G.inv_m) * w;
                     crgb[0] = fmaf(w, rc[R_RGB], crgb[0]);

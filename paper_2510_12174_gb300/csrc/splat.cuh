@@ -85,8 +85,10 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 // and the normal.  With v_s = -S^-1 Q p_c, d_s = S^-1 Q d~ (Q = R^T R_cw,
 // M_c = S^-1 Q) and p_c = z m~ (m~ = the centre's ray, m~_z = 1):
 //   v_s x d_s = det(S^-1) S Q (d~ x p_c) = kappa (.) M_c (Delta x m~),
-// Delta = d~ - m~ = ((u - m_x)/fx, (v - m_y)/fy, 0) from the exactly formed
-// pixel offset of the splat, kappa_a = z s_a / (s_b s_c): no cancellation.
+// Delta = d~ - m~ = ((u - m_x)/fx, (v - m_y)/fy, 0), kappa_a = z s_a / (s_b s_c).
+// Delta x m~ is linear in the exactly formed pixel offset (dx, dy) of the
+// splat, so the preprocess folds everything else into two vectors of the
+// record: cv = dx P1 + dy P2, no cancellation.
 // Square root by the approximate hardware instruction (a few ulp; subnormal
 // inputs supported): the pair geometry feeds tolerance-checked outputs only.
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -101,10 +103,9 @@ struct PairGeom {
 };
 
 // dxp, dyp: the pixel offset from the projected centre (splat_alpha's
-// outputs); ifx, ify: 1/fx, 1/fy.
+// outputs).
 __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, float xt, float yt,
-                                              float dxp, float dyp, float ifx, float ify,
-                                              PairGeom& G) {
+                                              float dxp, float dyp, PairGeom& G) {
     const float* M = rc + R_MC;
     const float* vs = rc + R_VS;
 #pragma unroll
@@ -113,13 +114,8 @@ __device__ __forceinline__ void pair_geometry(const float* __restrict__ rc, floa
     G.bp = fmaf(vs[0], G.ds[0], fmaf(vs[1], G.ds[1], vs[2] * G.ds[2]));
     const float inv_a = __fdividef(1.f, G.a);  // a = |d_s|^2 > 0, far below 2^126
     G.t = -G.bp * inv_a;
-    {
-        const float Dx = dxp * ifx, Dy = dyp * ify;
-        const float w0 = Dy, w1 = -Dx, w2 = fmaf(Dx, yt, -Dy * xt);  // Delta x m~
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            G.cv[i] = rc[R_KAP + i] * fmaf(M[3 * i], w0, fmaf(M[3 * i + 1], w1, M[3 * i + 2] * w2));
-    }
+    for (int i = 0; i < 3; ++i) G.cv[i] = fmaf(dxp, rc[R_P1 + i], dyp * rc[R_P2 + i]);
     const float cc = fmaf(G.cv[0], G.cv[0], fmaf(G.cv[1], G.cv[1], G.cv[2] * G.cv[2]));
     G.disc = G.a - cc;
     // d_s and cv are orthogonal, so the cross product does not cancel

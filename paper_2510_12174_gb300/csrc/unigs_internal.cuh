@@ -36,14 +36,16 @@ constexpr int TILE_PIX = TILE * TILE;
 //   [34..36] low words of the conic (double-float A, B, C)
 //   [37]    k (gradient factor)
 //   [38..40] RGB
-//   [41..43] kappa_a = z s_a / (s_b s_c): v_s x d_s = kappa (.) M_c (Delta x m~)
-//           (see pair_geometry), the cancellation-free form of the cross
-//           product for Gaussians far from the camera
+//   [41..43] P1, [44..46] P2: v_s x d_s = dx P1 + dy P2 for the pixel offset
+//           (dx, dy) from the projected centre (see pair_geometry), the
+//           cancellation-free form of the cross product for Gaussians far
+//           from the camera
+//   [47]    unused (keeps the record a whole number of 16-byte words)
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_CON = 4, R_OP = 7, R_EXTX = 8, R_EXTY = 9,
     R_FLAG = 10, R_SR = 11, R_MC = 12, R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34,
-    R_K = 37, R_RGB = 38, R_KAP = 41, REC_FLOATS = 44
+    R_K = 37, R_RGB = 38, R_P1 = 41, R_P2 = 44, R_PAD = 47, REC_FLOATS = 48
 };
 
 // Pixel of thread tid inside its 16x16 tile: warp w covers the 8x4 block at
