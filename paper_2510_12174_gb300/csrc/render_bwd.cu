@@ -24,6 +24,8 @@
 // (supplement Sec. 2: dL/ds_k = -(g_vs,k v_s,k + g_ds,k d_s,k)/s_k per ray,
 // dL/dmu = -R (g_vs / s)); colour -> SH coefficients and viewing direction;
 // then R(q^) -> q^ -> q through the tangent projection (I - q^ q^T)/|q|.
+#include <type_traits>
+
 #include "launch.h"
 #include "sh.cuh"
 #include "splat.cuh"
@@ -79,14 +81,42 @@ __device__ __forceinline__ int go_index(int p, int c) {
     return p * NS + ((((c >> 2) ^ p) & (NS / 4 - 1)) << 2) + (c & 3);
 }
 
-// dot(gO row p, semantic row) with 16-byte shared-memory loads and packed
-// float32 FMAs (four partial sums, one per channel residue mod 4).
+// f(integral_constant<int, I>) for I = 0 .. N-1, unrolled at compile time.
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// 16-byte shared-memory load at a 32-bit shared address plus a constant.
+template <int OFF>
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr), "n"(OFF));
+    return v;
+}
+
+// Shared address of chunk 0 of upstream-gradient row p with the row's swizzle
+// key folded in: the tile and its rows (NS floats) are aligned to the row
+// size, so chunk c of the row is at go_row(p) ^ (16 c).
 template <int NS>
-__device__ __forceinline__ float sem_dot(const float* go, int p, const float* row) {
+__device__ __forceinline__ uint32_t go_row(uint32_t go_base, int p) {
+    return (go_base + (uint32_t)(p * NS * 4)) | ((uint32_t)(p & (NS / 4 - 1)) << 4);
+}
+
+// dot(gO row, semantic row) with 16-byte shared-memory loads and packed
+// float32 FMAs (four partial sums, one per channel residue mod 4); a_row from
+// go_row.
+template <int NS>
+__device__ __forceinline__ float sem_dot(uint32_t a_row, const float* row) {
     float2 acc01 = make_float2(0.f, 0.f), acc23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < NS / 4; ++c) {
-        const float4 a = *reinterpret_cast<const float4*>(go + go_index<NS>(p, 4 * c));
+        const float4 a = lds128<0>(a_row ^ (uint32_t)(c << 4));
         const float4 b = reinterpret_cast<const float4*>(row)[c];
         acc01 = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), acc01);
         acc23 = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), acc23);
@@ -143,6 +173,15 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         fence_mbar_init();
     }
     for (int j = tid; j < 2 * B * NS; j += 256) (&S.sem[0][0][0])[j] = 0.f;
+    // the upstream-gradient rows are addressed by XOR within a row, which
+    // needs the tile aligned to the row size (it sits at a multiple of 256
+    // bytes of the dynamic shared memory, whose start is so aligned)
+    const uint32_t go_base = smem_u32(S.gO);
+    if (go_base & (uint32_t)(NS * 4 - 1)) {
+        if (tid == 0) set_status(P.hdr, UNIGS_ERR_CUDA);
+        return;
+    }
+    const uint32_t a_row = go_row<NS>(go_base, tid);
     __syncthreads();
     uint32_t loads[2] = {0u, 0u};  // completed loads per buffer (uniform)
     uint32_t used[2] = {0u, 0u};   // completed consumptions per buffer (uniform)
@@ -240,10 +279,14 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 if (!__any_sync(0xffffffffu, contrib)) continue;
                 float gv[32];
                 const float om = 1.f - alpha;
-                // om >= 1 - alpha_max: one approximate reciprocal serves the
-                // transmittance restoration and dL/dalpha
+                // om >= 1 - alpha_max.  The restoration T <- T / om runs along
+                // the whole list, so it keeps the correctly rounded division
+                // (with an approximate quotient the worst cancelling rotation
+                // gradient of a 200k-Gaussian test scene drifted 2.5x further
+                // from the float64 reference); dL/dalpha takes an approximate
+                // reciprocal
                 const float rom = __fdividef(1.f, om);
-                if (contrib) T = T * rom;
+                if (contrib) T = __fdiv_rn(T, om);
                 const float w = contrib ? alpha * T : 0.f;
                 PairGeom G;
                 pair_geometry(rc, xt, yt, dx, dy, G);
@@ -256,7 +299,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 const float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
                                  g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
                                  sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
-                                 sem_dot<NS>(S.gO, tid, &S.sem[buf][j][0]);
+                                 sem_dot<NS>(a_row, &S.sem[buf][j][0]);
                 const float dL_da = contrib ? T * Gi - Sacc * rom : 0.f;
                 Sacc = fmaf(w, Gi, Sacc);
                 // alpha = min(alpha_max, op * Gs)
@@ -359,17 +402,22 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                             S.wv[warp][lane] = make_float2(w, w);
                             __syncwarp();
                             const int h = lane / LPR, c4 = lane % LPR;
-                            const float* rowbase = S.gO + (warp * 32 + h) * NS;
+                            // row r = i RPS + h holds channel chunk c4 at chunk
+                            // c4 ^ (h % LPR) ^ ((i RPS) % LPR): the first part is
+                            // folded into the lane's base address, the second
+                            // repeats with i and is a constant
+                            const uint32_t a_g =
+                                (go_base + (uint32_t)((warp * 32 + h) * NS * 4)) |
+                                ((uint32_t)(c4 ^ (h & (LPR - 1))) << 4);
                             float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
-#pragma unroll
-                            for (int i = 0; i < LPR; ++i) {
-                                const int r = i * RPS + h;
-                                const float2 wr = S.wv[warp][r];
-                                const float4 go = *reinterpret_cast<const float4*>(
-                                    rowbase + i * RPS * NS + ((c4 ^ (r & (LPR - 1))) << 2));
+                            static_for<0, LPR>([&](auto ic) {
+                                constexpr int i = decltype(ic)::value;
+                                const float2 wr = S.wv[warp][i * RPS + h];
+                                const float4 go = lds128<i * RPS * NS * 4>(
+                                    a_g ^ (uint32_t)(((i * RPS) & (LPR - 1)) << 4));
                                 a01 = __ffma2_rn(wr, make_float2(go.x, go.y), a01);
                                 a23 = __ffma2_rn(wr, make_float2(go.z, go.w), a23);
-                            }
+                            });
 #pragma unroll
                             for (int o = LPR; o < 32; o <<= 1) {
                                 a01 = __fadd2_rn(a01, make_float2(
@@ -617,6 +665,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
 
 template <int NS, int B>
 static void launch_bwd_t(const BwdParams& P, int grid, cudaStream_t st) {
+    using Smem = BwdSmem<NS, B>;
+    static_assert(offsetof(Smem, gO) % 256 == 0,
+                  "the upstream-gradient tile must sit at a multiple of 256 bytes");
     const size_t smem = sizeof(BwdSmem<NS, B>);
     static bool attr_set = false;  // host-side, set once per instantiation
     if (!attr_set) {
