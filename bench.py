@@ -105,12 +105,12 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one render_bwd launch on this workload, from a
-# one-pass ncu capture of the full run (dram__bytes_read.sum 6.862 GB +
-# dram__bytes_write.sum 0.853 GB), valid only for the kernel sources whose
+# one-pass ncu capture of the full run (dram__bytes_read.sum 6.654 GB +
+# dram__bytes_write.sum 0.800 GB), valid only for the kernel sources whose
 # digest is recorded here; any change to them reports null until re-captured.
-BWD_TRAFFIC_BYTES = 7_715_647_232
+BWD_TRAFFIC_BYTES = 7_453_076_480
 BWD_TRAFFIC_SOURCES = ("render_bwd.cu", "splat.cuh", "unigs_internal.cuh", "ff.cuh", "sh.cuh")
-BWD_TRAFFIC_DIGEST = "70b940e685479961ccaa19c614fd46ddc76f96c75e6b4f4099b523f21024d13a"
+BWD_TRAFFIC_DIGEST = "a670a58b0e0a924aa25711b010d233c62c72830a898e092e0e21cc14d0e1e6c6"
 
 
 def bwd_traffic():
