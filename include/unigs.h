@@ -259,7 +259,10 @@ unigs_status unigs_render_bwd(const unigs_plan* plan, const unigs_gaussians* g,
                               unigs_stream stream);
 
 /* Reads the workspace status word (synchronises the stream).  *detail gets
- * the required instance count for UNIGS_ERR_CAPACITY. */
+ * the required instance count for UNIGS_ERR_CAPACITY.  Device-side values:
+ * UNIGS_ERR_CAPACITY, UNIGS_ERR_TIMEOUT, and UNIGS_ERR_CUDA when the
+ * backward composite finds its dynamic shared memory not aligned to its
+ * 256-byte row layout (the kernel then does no work). */
 unigs_status unigs_status_poll(const unigs_plan* plan, const void* ws, int64_t* detail,
                                unigs_stream stream);
 
