@@ -110,7 +110,7 @@ class ClockSampler:
 # digest is recorded here; any change to them reports null until re-captured.
 BWD_TRAFFIC_BYTES = 7_453_076_480
 BWD_TRAFFIC_SOURCES = ("render_bwd.cu", "splat.cuh", "unigs_internal.cuh", "ff.cuh", "sh.cuh")
-BWD_TRAFFIC_DIGEST = "a670a58b0e0a924aa25711b010d233c62c72830a898e092e0e21cc14d0e1e6c6"
+BWD_TRAFFIC_DIGEST = "b8bcfeaa8b7b6d041f522d09cceeef70397868f881d5109c3bde4fb73ae65d10"
 
 
 def bwd_traffic():

@@ -157,8 +157,8 @@ __device__ __forceinline__ void cross_acc(const float* a, const float* b, float*
 }
 
 template <int NS, int B>
-// batch 8 (71 KB of shared memory at 64 logits): 3 CTAs per SM, 80 registers;
-// larger batches (77 KB at 16, 90 KB at 32): 2 CTAs per SM, 128 registers
+// batch 8 (73 KB of shared memory at 64 logits): 3 CTAs per SM, 80 registers;
+// larger batches (80 KB at 16, 94 KB at 32): 2 CTAs per SM, 128 registers
 __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const BwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BwdSmem<NS, B>& S = *reinterpret_cast<BwdSmem<NS, B>*>(smem_raw);

@@ -99,7 +99,7 @@ __device__ __forceinline__ void tc_issue_batch(const FwdTcParams& P, FwdTcSmem<N
 }
 
 template <int NS, int B, bool F32>
-// batch 16: 45 KB of shared memory and <= 64 registers, 4 CTAs per SM (4 x
+// batch 16: 47 KB of shared memory and <= 64 registers, 4 CTAs per SM (4 x
 // 128 accumulator columns fill the tensor memory); larger batches: 2
 __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(const FwdTcParams P) {
     using Sm = FwdTcSmem<NS, B, F32>;

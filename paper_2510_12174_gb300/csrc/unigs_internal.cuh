@@ -14,7 +14,7 @@ constexpr int TILE_PIX = TILE * TILE;
 
 // ----------------------------------------------------------------------------
 // Per-(camera, Gaussian) forward record written by the preprocess and staged
-// into shared memory by the composite kernels (44 floats = 176 bytes, a
+// into shared memory by the composite kernels (48 floats = 192 bytes, a
 // multiple of 16 so a bulk copy can move it).  The fields every evaluated
 // (pixel, Gaussian) pair reads (warp box test and alpha) fill the first three
 // 16-byte words.
