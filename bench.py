@@ -122,6 +122,22 @@ def bwd_traffic():
     return BWD_TRAFFIC_BYTES if h.hexdigest() == BWD_TRAFFIC_DIGEST else None
 
 
+def hbm_bytes_per_step(n: int, sh_degree: int, n_sem: int, pixels: int, instances: int,
+                       feat_bytes: int) -> int:
+    """Algorithmic HBM bytes of one batched forward + backward step: every
+    parameter read once in each pass (P twice), each parameter gradient written
+    once (G), each output (O) and upstream gradient (U, plus the
+    normal-from-depth gradient) touched once, and 44 B per (tile, Gaussian)
+    instance (written, sorted once, read by both composites).  P and G are paid
+    once for all views of the step; pixels is the total over the views."""
+    n_sh = (sh_degree + 1) ** 2
+    P = n * (48 + (3 * n_sh + n_sem) * feat_bytes)
+    G = n * (12 + 3 * n_sh + n_sem) * 4
+    O = pixels * (8 + n_sem + 2) * 4
+    U = pixels * (8 + n_sem) * 4 + 3 * pixels * 4
+    return 2 * P + G + O + U + 44 * instances
+
+
 def launch_shape(cfg, simt_logits: bool) -> dict:
     """The composites' launch shapes after the library's defaults."""
     bwd = (int(cfg.batch) or 8, int(cfg.ctas_per_sm) or 3)
@@ -425,6 +441,15 @@ def run_ours(args):
         "gpu_launches": r.launches_per_step() * args.steps,
         "clocks": clocks,
     }
+    hbm_b = hbm_bytes_per_step(args.n_gauss, sc.sh_degree, n_sem,
+                               sum(c.width * c.height for c in cams), n_inst, 2)
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    line["hbm_view"] = {"bytes_per_step": hbm_b,
+                        "achieved_gbs": hbm_b / (ms_all / 1000.0) / 1e9 * world,
+                        "peak_gbs": hbm_peak,
+                        "frac": hbm_b / (ms_all / 1000.0) / 1e9 * world / hbm_peak,
+                        "note": "algorithmic bytes of the whole step against the measured "
+                                "copy bandwidth; the step is ALU/issue-bound (see roofline)"}
     if not args.skip_train:
         del graph, r, out, grads, gbuf, dev_up
         torch.cuda.synchronize()
