@@ -230,7 +230,8 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
                    normal=torch.zeros(P, 3, dtype=F64), kmap=z.clone(),
                    logits=torch.zeros(P, C, dtype=F64), T=torch.ones(P, dtype=F64),
                    n_contrib=torch.zeros(P, dtype=torch.int64),
-                   n_used=torch.zeros(P, dtype=torch.int64))
+                   n_used=torch.zeros(P, dtype=torch.int64),
+                   stats_eval=torch.zeros(P, dtype=torch.int64))
         for k in ("amb_fwd", "amb_grad"):
             out[k] = torch.zeros(P, dtype=torch.bool)
         out["decisions"] = None
