@@ -16,6 +16,9 @@
  * - Every pointer argument marked "device" is caller-owned device memory.
  *   The library never allocates or frees memory and keeps no global mutable
  *   state; the caller allocates one workspace of unigs_workspace_bytes().
+ *   The one exception is unigs_sort_pairs_static (end of this header): its
+ *   scratch is a static device array of the library, shared by every call,
+ *   with a process-wide cache of that array's address per device.
  * - All calls are asynchronous on the given CUDA stream, except
  *   unigs_bin_sort() with a non-NULL n_instances_out and unigs_status_poll(),
  *   which synchronise that stream.
@@ -55,7 +58,8 @@ typedef enum {
     UNIGS_ERR_INVALID_ARG = 1, /* host-side argument check failed               */
     UNIGS_ERR_CAPACITY = 2,    /* more (tile, Gaussian) instances than capacity  */
     UNIGS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed    */
-    UNIGS_ERR_NONFINITE = 4,   /* reserved: non-finite input detected             */
+    UNIGS_ERR_NONFINITE = 4,   /* a parameter array holds a NaN or an infinity
+                                  (UNIGS_FLAG_CHECK_FINITE)                       */
     UNIGS_ERR_TIMEOUT = 5      /* a bounded device wait ran out                  */
 } unigs_status;
 
@@ -149,7 +153,10 @@ typedef struct {
                              ablation of Tab. 6); bit 1:
                              UNIGS_FLAG_SIMT_LOGITS (blend the logits on the
                              FP32 pipes even where the tensor-core blend
-                             applies) */
+                             applies); bit 2: UNIGS_FLAG_CHECK_FINITE
+                             (unigs_preprocess scans every parameter array
+                             and records UNIGS_ERR_NONFINITE in the status
+                             word if one holds a NaN or an infinity) */
     int32_t batch;        /* Gaussians staged per batch by the backward
                              composite: 8, 16, 32 or 64 (0 = 8) */
     int32_t ctas_per_sm;  /* persistent backward CTAs per SM, 1..8 (0 = 3) */
@@ -162,6 +169,7 @@ typedef struct {
 
 #define UNIGS_FLAG_CENTER_DEPTH 1u
 #define UNIGS_FLAG_SIMT_LOGITS 2u
+#define UNIGS_FLAG_CHECK_FINITE 4u
 
 /* Host-side plan: sizes and workspace offsets for one (Gaussians, cameras)
  * configuration.  Filled by unigs_plan_init; owned by the caller; read-only
@@ -199,7 +207,10 @@ size_t unigs_workspace_bytes(const unigs_plan* plan);
  * per-Gaussian ray-ellipsoid setup of Sec. 3.2 (v_s = S^-1 R^T (C - mu) and
  * the camera-ray map S^-1 R^T R_cw) and the depth key.  The tile rectangle
  * and key follow an explicit float32 recipe (bit-reproducible).  Also clears
- * the workspace status word.  cams: host array of plan->n_cams cameras. */
+ * the workspace status word.  cams: host array of plan->n_cams cameras.
+ * With UNIGS_FLAG_CHECK_FINITE it first scans the Gaussian arrays for NaN
+ * and infinity (UNIGS_ERR_NONFINITE in the status word; the stages still run,
+ * and a non-finite input then gives non-finite outputs, never a hang). */
 unigs_status unigs_preprocess(const unigs_plan* plan, const unigs_gaussians* g,
                               const unigs_camera* cams, void* ws, unigs_stream stream);
 
@@ -259,8 +270,11 @@ unigs_status unigs_render_bwd(const unigs_plan* plan, const unigs_gaussians* g,
                               unigs_stream stream);
 
 /* Reads the workspace status word (synchronises the stream).  *detail gets
- * the required instance count for UNIGS_ERR_CAPACITY.  Device-side values:
- * UNIGS_ERR_CAPACITY, UNIGS_ERR_TIMEOUT, and UNIGS_ERR_CUDA when the
+ * the required instance count for UNIGS_ERR_CAPACITY, and for
+ * UNIGS_ERR_NONFINITE the first array found non-finite (0 mean, 1 quat,
+ * 2 scale, 3 opacity, 4 kfac, 5 sh, 6 sem).  Device-side values:
+ * UNIGS_ERR_CAPACITY, UNIGS_ERR_NONFINITE, UNIGS_ERR_TIMEOUT, and
+ * UNIGS_ERR_CUDA when the
  * backward composite finds its dynamic shared memory not aligned to its
  * 256-byte row layout (the kernel then does no work). */
 unigs_status unigs_status_poll(const unigs_plan* plan, const void* ws, int64_t* detail,
@@ -289,13 +303,16 @@ const char* unigs_status_string(unigs_status s);
  * the key - the sort unigs_bin_sort runs on the tile|depth keys - but with its
  * scratch memory (one ping-pong buffer, digit histograms, scan partials, a
  * status block) in a static device array of the library rather than in a
- * caller workspace.  The caller passes device inputs and outputs only; the
- * outputs must not overlap the inputs.  Sorted order: ascending key, ties in
- * input order.
+ * caller workspace.  The caller passes device inputs and outputs only.
+ * Sorted order: ascending (key mod 2^key_bits), ties in input order; key
+ * bits at and above key_bits may hold anything and never decide the order
+ * (the last 8-bit pass is masked to the bits that remain), and the output
+ * keys are the input keys unchanged.
  *
  * Limits and behaviour: n <= UNIGS_STATIC_SORT_MAX_PAIRS (2^20); larger n,
- * key_bits outside 1..64, or NULL / aliased buffers return
- * UNIGS_ERR_INVALID_ARG before anything runs.  The static array (about
+ * key_bits outside 1..64, NULL buffers, or an output that shares a byte with
+ * an input or with the other output return UNIGS_ERR_INVALID_ARG before
+ * anything runs.  The static array (about
  * 12.5 MB) is held by every GPU that loads the library until the process
  * exits.  The first call on a device (with that device current, and the
  * stream on that device) looks up the array's device address; make that
@@ -306,6 +323,21 @@ const char* unigs_status_string(unigs_status s);
 unigs_status unigs_sort_pairs_static(const unsigned long long* keys_in, const uint32_t* vals_in,
                                      int64_t n, int32_t key_bits, unsigned long long* keys_out,
                                      uint32_t* vals_out, unigs_stream stream);
+
+/* FP32 FMA throughput probe (a measurement utility; the paper has no
+ * counterpart).  The composite kernels are bound by FP32 arithmetic, so their
+ * roofline is taken against the FMA rate measured on the GPU in use.  Launches
+ * one kernel of 8 CTAs x 256 threads per SM, each thread running 8 independent
+ * FMA chains of 16 * iters steps, as scalar FMAs (packed = 0) or as packed
+ * float32-pair FMAs (packed = 1, two FMAs per instruction).  sink: device
+ * buffer of at least unigs_probe_fma_sink_floats() floats (caller-owned,
+ * receives one value per thread).  *flops_out (host, may be NULL) gets the
+ * floating-point operations of the launch (an FMA counts 2).  The caller
+ * times the launch on its stream.  Returns UNIGS_ERR_INVALID_ARG for a NULL
+ * sink, iters < 1 or packed outside 0..1, UNIGS_ERR_CUDA if the launch fails. */
+int64_t unigs_probe_fma_sink_floats(void);
+unigs_status unigs_probe_fma(float* sink, int32_t iters, int32_t packed, int64_t* flops_out,
+                             unigs_stream stream);
 
 #ifdef __cplusplus
 }

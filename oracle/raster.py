@@ -197,15 +197,76 @@ def ray_ellipsoid(R: torch.Tensor, s: torch.Tensor, v_s: torch.Tensor,
     return depth, n, disc, qa, qc
 
 
+U32 = 2.0 ** -24          # unit roundoff of float32
+EXP2_APPROX = 2.0 ** -21  # relative error allowed for the hardware exp2 approximation
+KAPPA_SPLIT = 65.0        # conic eigenvalue ratio above which the kernels evaluate the
+                          # quadratic form in double-float (64, plus a margin for their
+                          # float32 estimate of the ratio)
+
+
 @dataclasses.dataclass
 class Bands:
-    """Relative widths of the bands around each discrete decision."""
-    alpha: float = 3e-4     # alpha vs 1/255
-    T: float = 2e-4         # T (1 - alpha) vs 1e-4
-    inside: float = 1e-5    # c = v_s.v_s - 1 vs 0
-    disc: float = 1e-5      # (b^2-4ac)/(4a^2) vs 0: normal precision
-    clamp: float = 1e-5     # alpha vs 0.99 (gradient kink only)
-    disc_grad: float = 2e-3  # singular normal gradient near the silhouette
+    """Widths of the bands around each discrete decision (test infrastructure:
+    where a float64 decision lies inside its band, a float32 evaluation may
+    decide the other way, so the pixel is not compared element-wise).
+
+    ``alpha`` and ``T`` default to None: the width is then the first-order
+    float32 error bound of the kernels' evaluation, per (pixel, Gaussian)
+    pair for alpha and accumulated along the list for T (see
+    :func:`alpha_error_bound`); a float gives a fixed relative width instead.
+    ``inside`` bounds |c| = |v_s.v_s - 1| (camera inside the 1-sigma
+    ellipsoid).  ``disc`` and ``disc_grad`` bound the relative discriminant
+    delta = disc/a of the ray-ellipsoid quadratic: the kernels form
+    disc = a - |v_s x d_s|^2 from float32 record entries, so near the
+    silhouette (delta -> 0) disc carries an absolute error of about 4 u a.
+    The normal moves like sqrt(disc), so its float32 error is about
+    2 u / sqrt(delta): below 1e-4 for delta >= 1e-5 (``disc``).  Its
+    derivative carries 1/sqrt(disc): a pair's gradient term is about
+    delta^-1/2 times an ordinary one and off by 2 u / delta relative, i.e.
+    2 u delta^-3/2 of an ordinary term, which stays below 1e-4 for
+    delta >= 1e-2 (``disc_grad``).  ``clamp`` is a fixed width for alpha vs
+    alpha_max when ``alpha`` is fixed."""
+    alpha: Optional[float] = None
+    T: Optional[float] = None
+    inside: float = 1e-5
+    disc: float = 1e-5
+    clamp: float = 1e-5
+    disc_grad: float = 1e-2
+
+
+def alpha_error_bound(con: torch.Tensor, dx: torch.Tensor, dy: torch.Tensor,
+                      kappa: torch.Tensor) -> torch.Tensor:
+    """First-order relative error bound of a float32 evaluation of
+    alpha = opacity * exp(-q/2), q = D^T K D, as the composite kernels do it.
+
+    con [L,3] conic (A, B, C), dx, dy [P,L] pixel offsets, kappa [L] the
+    conic's eigenvalue ratio.  With S = A dx^2 + C dy^2 + 2|B dx dy| (the sum
+    of the absolute terms of q) and u = 2^-24:
+      * float32 quadratic form (kappa <= KAPPA_SPLIT): rounding the conic to
+        float32 and the three products and two additions give
+        |dq| <= 4 u S (6 u S taken); double-float form otherwise: |dq| <= u q
+        (the final rounding);
+      * exp(-q/2) then carries a relative error q/2 * |dq|/q, plus q u from
+        the rounded product x log2(e) inside the hardware exp, plus the exp2
+        approximation (2^-21 taken);
+      * the product with the opacity rounds once more (u).
+    So beta = u (3 S + q + 1) + 2^-21 on the float32 path and
+    u (1.5 q + 1) + 2^-21 on the double-float path."""
+    q = con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy + 2.0 * con[None, :, 1] * dx * dy
+    S = con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy \
+        + 2.0 * (con[None, :, 1] * dx * dy).abs()
+    f32_path = (kappa <= KAPPA_SPLIT)[None, :]
+    beta32 = U32 * (3.0 * S + q + 1.0)
+    betaff = U32 * (1.5 * q + 1.0)
+    return torch.where(f32_path, beta32, betaff) + EXP2_APPROX
+
+
+def conic_ratio(con: torch.Tensor) -> torch.Tensor:
+    """Eigenvalue ratio lambda_max / lambda_min of the conics [L,3]."""
+    a, b, c = con.unbind(-1)
+    half = 0.5 * (a + c)
+    rad = torch.sqrt(0.25 * (a - c) ** 2 + b * b)
+    return (half + rad) / (half - rad)
 
 
 def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
@@ -279,12 +340,29 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
         out["n_contrib"] = torch.where(incl, pos, torch.zeros_like(pos)).max(1).values
         out["n_used"] = incl.sum(1)
         evaluated = T_before >= T_MIN
-        amb_alpha = (evaluated & ((alpha - ALPHA_MIN).abs() <= bands.alpha * ALPHA_MIN)).any(1)
-        amb_T = (evaluated & valid & ((T_after - T_MIN).abs() <= bands.T * T_MIN)).any(1)
+        # widths of the alpha and T bands: the float32 error bound of the
+        # kernels' evaluation (Bands), or fixed relative widths
+        if bands.alpha is None:
+            beta = alpha_error_bound(con.detach(), dx.detach(), dy.detach(),
+                                     conic_ratio(con.detach()))
+        else:
+            beta = torch.full_like(alpha, bands.alpha)
+        clamp_w = beta if bands.alpha is None else torch.full_like(alpha, bands.clamp)
+        if bands.T is None:
+            # T after j blends: each blended alpha_j moves it by
+            # alpha_j beta_j / (1 - alpha_j) (relative), and each product
+            # 1 - alpha, T (1 - alpha) rounds twice
+            ae = a_eff.detach()
+            step = torch.where(valid, ae * beta / (1.0 - ae) + 2.0 * U32, torch.zeros_like(ae))
+            beta_T = torch.cumsum(step, dim=1)
+        else:
+            beta_T = torch.full_like(alpha, bands.T)
+        amb_alpha = (evaluated & ((alpha - ALPHA_MIN).abs() <= beta * alpha)).any(1)
+        amb_T = (evaluated & valid & ((T_after - T_MIN).abs() <= beta_T * T_after)).any(1)
         amb_in = (incl & (qc.abs() <= bands.inside)[None, :]).any(1)
         rel_disc = disc / qa
         amb_disc = (incl & (rel_disc.abs() <= bands.disc)).any(1)
-        amb_clamp = (incl & ((a_raw - ALPHA_MAX).abs() <= bands.clamp)).any(1)
+        amb_clamp = (incl & ((a_raw - ALPHA_MAX).abs() <= clamp_w * a_raw)).any(1)
         amb_dg = (incl & (rel_disc.abs() <= bands.disc_grad)).any(1)
         out["amb_fwd"] = amb_alpha | amb_T | amb_in | amb_disc
         out["amb_grad"] = out["amb_fwd"] | amb_clamp | amb_dg

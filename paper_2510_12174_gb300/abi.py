@@ -19,6 +19,7 @@ UNIGS_TILE = 16
 UNIGS_MAX_SEM = 64
 UNIGS_FLAG_CENTER_DEPTH = 1
 UNIGS_FLAG_SIMT_LOGITS = 2
+UNIGS_FLAG_CHECK_FINITE = 4
 UNIGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 
 UNIGS_OK = 0
@@ -144,6 +145,8 @@ _SIGS = [
     ("unigs_status_string", c_char_p, [c_int32]),
     ("unigs_sort_pairs_static", c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                           c_void_p, c_void_p]),
+    ("unigs_probe_fma_sink_floats", c_int64, []),
+    ("unigs_probe_fma", c_int32, [c_void_p, c_int32, c_int32, POINTER(c_int64), c_void_p]),
     # include/unigs_train.h
     ("unigs_loss_lambda_default", None, [POINTER(unigs_loss_lambda)]),
     ("unigs_loss", c_int32, [POINTER(unigs_plan), POINTER(unigs_outputs), c_void_p,
@@ -256,6 +259,15 @@ def unigs_sort_pairs_static(keys_in, vals_in, n, key_bits, keys_out, vals_out, s
     array (see include/unigs.h)."""
     return lib().unigs_sort_pairs_static(keys_in, vals_in, n, key_bits, keys_out, vals_out,
                                          stream)
+
+
+def unigs_probe_fma_sink_floats() -> int:
+    return lib().unigs_probe_fma_sink_floats()
+
+
+def unigs_probe_fma(sink, iters, packed, flops_out, stream) -> int:
+    """FP32 FMA throughput probe (measurement utility, include/unigs.h)."""
+    return lib().unigs_probe_fma(sink, iters, packed, flops_out, stream)
 
 
 def unigs_launches_per_step(plan) -> int:

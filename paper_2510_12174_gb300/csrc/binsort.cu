@@ -214,10 +214,12 @@ __device__ __forceinline__ uint32_t n_valid(const WsHeader* hdr) {
     return hdr->status == UNIGS_ERR_CAPACITY ? 0u : hdr->n_instances;
 }
 
-// Per-block digit counts, stored digit-major: hist[d * nb + b].
+// Per-block digit counts, stored digit-major: hist[d * nb + b].  The digit of
+// a key is (key >> shift) & dmask (dmask 255 for a whole byte; fewer bits on
+// a last pass that must ignore the key bits above the sorted ones).
 __global__ void __launch_bounds__(256)
     radix_hist_kernel(const unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr,
-                      int shift, int nb, uint32_t* __restrict__ hist) {
+                      int shift, uint32_t dmask, int nb, uint32_t* __restrict__ hist) {
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(256)
     const int64_t base = (int64_t)blockIdx.x * SORT_ITEMS;
     for (int j = threadIdx.x; j < SORT_ITEMS; j += 256) {
         const int64_t i = base + j;
-        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & dmask], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256)
     radix_scatter_kernel(const unsigned long long* __restrict__ kin,
                          const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
                          uint32_t* __restrict__ vout, const uint32_t* __restrict__ scanned,
-                         const WsHeader* __restrict__ hdr, int shift, int nb) {
+                         const WsHeader* __restrict__ hdr, int shift, uint32_t dmask, int nb) {
     __shared__ uint32_t whist[8][256];
     __shared__ uint32_t goff[256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(256)
         const bool ok = i < n;
         k[it] = ok ? kin[i] : 0ull;
         v[it] = ok ? vin[i] : 0u;
-        const uint32_t d = ok ? ((uint32_t)(k[it] >> shift) & 255u) : 256u;
+        const uint32_t d = ok ? ((uint32_t)(k[it] >> shift) & dmask) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = (d < 256u) ? whist[w][d] : 0u;
         __syncwarp();
@@ -332,10 +334,10 @@ __global__ void __launch_bounds__(1024)
 
 int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long long* kout,
                uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
-               int shift, int nb, cudaStream_t st) {
-    radix_hist_kernel<<<nb, 256, 0, st>>>(kin, hdr, shift, nb, hist);
+               int shift, uint32_t dmask, int nb, cudaStream_t st) {
+    radix_hist_kernel<<<nb, 256, 0, st>>>(kin, hdr, shift, dmask, nb, hist);
     int launches = 1 + scan_u32(hist, (int64_t)nb * 256, scan_tmp, hist, nullptr, st);
-    radix_scatter_kernel<<<nb, 256, 0, st>>>(kin, vin, kout, vout, hist, hdr, shift, nb);
+    radix_scatter_kernel<<<nb, 256, 0, st>>>(kin, vin, kout, vout, hist, hdr, shift, dmask, nb);
     return launches + 1;
 }
 
@@ -370,10 +372,10 @@ int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
     uint32_t* hist = ws_ptr<uint32_t>(ws, p, OFF_HIST);
     for (int pass = 0; pass < p.sort_passes; ++pass) {
         const int src = pass & 1, dst = src ^ 1;
-        radix_hist_kernel<<<nb, 256, 0, st>>>(keys[src], hdr, 8 * pass, nb, hist);
+        radix_hist_kernel<<<nb, 256, 0, st>>>(keys[src], hdr, 8 * pass, 255u, nb, hist);
         launches += 1 + scan_u32(hist, (int64_t)nb * 256, scan_tmp, hist, nullptr, st);
         radix_scatter_kernel<<<nb, 256, 0, st>>>(keys[src], vals[src], keys[dst], vals[dst], hist,
-                                                 hdr, 8 * pass, nb);
+                                                 hdr, 8 * pass, 255u, nb);
         ++launches;
     }
     const int fin = sorted_buffer(p);

@@ -1,6 +1,12 @@
 // C ABI of libunigs: plan, workspace layout, argument checks, entry points.
 #include <string.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 
 using namespace unigs;
@@ -18,9 +24,30 @@ int sm_count() {
     }
     return cached[dev];
 }
+
+cudaError_t ensure_smem_limit(const void* func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;  // (kernel, device)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(func, dev);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
 }  // namespace unigs
 
 namespace {
+
+// One NVTX range per entry point (host side: it brackets the launches the call
+// enqueues, so a profiler timeline shows the stages by name).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -114,7 +141,8 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
         !(plan->cfg.T_min >= 0.f && plan->cfg.T_min < 1.f) ||
         !(plan->cfg.lowpass >= 0.f && plan->cfg.lowpass < 1e30f))
         return UNIGS_ERR_INVALID_ARG;
-    if (plan->cfg.flags & ~(UNIGS_FLAG_CENTER_DEPTH | UNIGS_FLAG_SIMT_LOGITS))
+    if (plan->cfg.flags &
+        ~(UNIGS_FLAG_CENTER_DEPTH | UNIGS_FLAG_SIMT_LOGITS | UNIGS_FLAG_CHECK_FINITE))
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.batch != 0 && plan->cfg.batch != 8 && plan->cfg.batch != 16 &&
         plan->cfg.batch != 32 && plan->cfg.batch != 64)
@@ -172,7 +200,7 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     sizes[OFF_VALS1] = sizeof(uint32_t) * (size_t)cap;
     sizes[OFF_HIST] = sizeof(uint32_t) * 256 * (size_t)nb_sort;
     sizes[OFF_RANGES] = sizeof(uint2) * (size_t)tiles;
-    sizes[OFF_GREC] = sizeof(float) * GREC_FLOATS * (size_t)total;
+    sizes[OFF_GREC] = sizeof(double) * GREC_FLOATS * (size_t)total;
     sizes[OFF_CULL] = sizeof(float) * CULL_FLOATS * (size_t)total;
     // float32 copy of bfloat16 semantic rows, refreshed by every preprocess
     sizes[OFF_SEM32] = g->feat_dtype ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
@@ -191,6 +219,7 @@ size_t unigs_workspace_bytes(const unigs_plan* plan) { return plan ? plan->ws_by
 
 unigs_status unigs_preprocess(const unigs_plan* plan, const unigs_gaussians* g,
                               const unigs_camera* cams, void* ws, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_preprocess");
     if (!plan || !cams || !ws || !aligned16(ws) || !check_gauss(plan, g))
         return UNIGS_ERR_INVALID_ARG;
     static thread_local CamTable tab;
@@ -201,6 +230,7 @@ unigs_status unigs_preprocess(const unigs_plan* plan, const unigs_gaussians* g,
 
 unigs_status unigs_bin_sort(const unigs_plan* plan, void* ws, int64_t* n_instances_out,
                             unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_bin_sort");
     if (!plan || !ws || !aligned16(ws)) return UNIGS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     launch_bin_sort(*plan, ws, st);
@@ -218,6 +248,7 @@ unigs_status unigs_bin_sort(const unigs_plan* plan, void* ws, int64_t* n_instanc
 
 unigs_status unigs_render_fwd(const unigs_plan* plan, const unigs_gaussians* g, void* ws,
                               const unigs_outputs* out, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_render_fwd");
     if (!plan || !ws || !out || !check_gauss(plan, g)) return UNIGS_ERR_INVALID_ARG;
     if (!out->rgb || !out->depth || !out->normal_g || !out->kmap || !out->T_final ||
         !out->n_contrib || (plan->n_sem > 0 && !out->logits))
@@ -228,6 +259,7 @@ unigs_status unigs_render_fwd(const unigs_plan* plan, const unigs_gaussians* g, 
 
 unigs_status unigs_depth_normal_fwd(const unigs_plan* plan, const unigs_camera* cams,
                                     const float* depth, float* normal_d, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_depth_normal_fwd");
     if (!plan || !cams || !depth || !normal_d) return UNIGS_ERR_INVALID_ARG;
     static thread_local CamTable tab;
     if (!build_cam_table(plan, cams, &tab)) return UNIGS_ERR_INVALID_ARG;
@@ -239,6 +271,7 @@ unigs_status unigs_depth_normal_bwd(const unigs_plan* plan, const unigs_camera* 
                                     const float* depth, const float* g_normal_d,
                                     const float* g_depth_in, float* g_depth_out,
                                     unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_depth_normal_bwd");
     if (!plan || !cams || !depth || !g_normal_d || !g_depth_out) return UNIGS_ERR_INVALID_ARG;
     static thread_local CamTable tab;
     if (!build_cam_table(plan, cams, &tab)) return UNIGS_ERR_INVALID_ARG;
@@ -251,6 +284,7 @@ unigs_status unigs_render_bwd(const unigs_plan* plan, const unigs_gaussians* g,
                               const unigs_camera* cams, void* ws, const unigs_outputs* fwd,
                               const unigs_grad_outputs* grad_out, unigs_param_grads* grads,
                               unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_render_bwd");
     (void)cams;
     if (!plan || !ws || !fwd || !grad_out || !grads || !check_gauss(plan, g))
         return UNIGS_ERR_INVALID_ARG;
@@ -265,11 +299,12 @@ unigs_status unigs_status_poll(const unigs_plan* plan, const void* ws, int64_t* 
     if (!plan || !ws) return UNIGS_ERR_INVALID_ARG;
     WsHeader h;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(&h, ws_ptr<WsHeader>(const_cast<void*>(ws), *plan, OFF_HDR), 32,
+    if (cudaMemcpyAsync(&h, ws_ptr<WsHeader>(const_cast<void*>(ws), *plan, OFF_HDR), 64,
                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return UNIGS_ERR_CUDA;
-    if (detail) *detail = (int64_t)h.need;
+    if (detail)
+        *detail = h.status == UNIGS_ERR_NONFINITE ? (int64_t)h.nonfinite : (int64_t)h.need;
     return (unigs_status)h.status;
 }
 
@@ -296,7 +331,9 @@ int32_t unigs_launches_per_step(const unigs_plan* plan) {
         const int64_t cnt = plan->n * (int64_t)plan->n_sem;
         conv = (cnt / 2 > 0 ? 1 : 0) + (int)(cnt & 1);
     }
-    return 2 /*preprocess*/ + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ + 2 /*bwd*/;
+    const int check = (plan->cfg.flags & UNIGS_FLAG_CHECK_FINITE) && plan->n > 0 ? 1 : 0;
+    return 2 /*preprocess*/ + check + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ +
+           2 /*bwd*/;
 }
 
 // ------------------------------------------------------------ training step
@@ -309,6 +346,7 @@ void unigs_loss_lambda_default(unigs_loss_lambda* lam) {
 unigs_status unigs_loss(const unigs_plan* plan, const unigs_outputs* out, const float* normal_d,
                         const unigs_targets* tgt, const unigs_loss_lambda* lambda, void* ws,
                         float* record, const unigs_loss_grads* grads, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_loss");
     if (!plan || !out || !tgt || !lambda || !ws || !record || !grads) return UNIGS_ERR_INVALID_ARG;
     if ((tgt->rgb && !out->rgb) || (tgt->depth && !out->depth) || (tgt->normal && !normal_d) ||
         (tgt->label && (!out->logits || plan->n_sem == 0)))
@@ -319,6 +357,7 @@ unigs_status unigs_loss(const unigs_plan* plan, const unigs_outputs* out, const 
 
 unigs_status unigs_adam_step(const unigs_adam_group* groups, int32_t n_groups,
                              const unigs_adam_hparams* hp, int32_t* step, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_adam_step");
     if (!hp || !step || n_groups < 0 || n_groups > UNIGS_ADAM_MAX_GROUPS ||
         (n_groups > 0 && !groups))
         return UNIGS_ERR_INVALID_ARG;
@@ -335,6 +374,7 @@ unigs_status unigs_adam_step(const unigs_adam_group* groups, int32_t n_groups,
 
 unigs_status unigs_param_copies(const unigs_adam_group* groups, int32_t n_groups,
                                 unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_param_copies");
     if (n_groups < 0 || n_groups > UNIGS_ADAM_MAX_GROUPS || (n_groups > 0 && !groups))
         return UNIGS_ERR_INVALID_ARG;
     for (int i = 0; i < n_groups; ++i) {
@@ -352,6 +392,7 @@ size_t unigs_prune_workspace_bytes(int64_t n) { return n < 0 ? 0 : prune_ws_byte
 
 unigs_status unigs_prune_mark(const float* k, int64_t n, float T_k, void* prune_ws,
                               int64_t* n_keep, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_prune_mark");
     if (n < 0 || n > 0xffffffffLL || (n > 0 && !k) || !prune_ws || !aligned16(prune_ws) || !n_keep)
         return UNIGS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -369,6 +410,7 @@ unigs_status unigs_prune_mark(const float* k, int64_t n, float T_k, void* prune_
 
 unigs_status unigs_prune_compact(const unigs_prune_array* arrays, int32_t n_arrays, int64_t n,
                                  int64_t n_keep, const void* prune_ws, unigs_stream stream) {
+    NvtxRange nvtx_range("unigs_prune_compact");
     if (n < 0 || n_keep < 0 || n_keep > n || n_arrays < 0 || (n_arrays > 0 && !arrays) ||
         !prune_ws)
         return UNIGS_ERR_INVALID_ARG;

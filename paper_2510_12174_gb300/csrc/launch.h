@@ -25,13 +25,15 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_outputs& fwd, const unigs_grad_outputs& go,
                       const unigs_param_grads& grads, cudaStream_t st);
 
-// One stable 8-bit LSD radix pass over the n = hdr->n_instances pairs (n read
-// on the device; 0 when hdr->status reports a capacity overflow): per-block
-// digit histograms, their exclusive scan, stable scatter.  nb blocks of
-// SORT_ITEMS pairs; hist holds 256 * nb counters, scan_tmp the scan partials.
+// One stable LSD radix pass over the n = hdr->n_instances pairs (n read on
+// the device; 0 when hdr->status reports a capacity overflow) on the digit
+// (key >> shift) & dmask (dmask 255 for a whole byte, 2^b - 1 to sort by b < 8
+// bits): per-block digit histograms, their exclusive scan, stable scatter.  nb
+// blocks of SORT_ITEMS pairs; hist holds 256 * nb counters, scan_tmp the scan
+// partials.
 int radix_pass(const unsigned long long* kin, const uint32_t* vin, unsigned long long* kout,
                uint32_t* vout, uint32_t* hist, uint32_t* scan_tmp, const WsHeader* hdr,
-               int shift, int nb, cudaStream_t st);
+               int shift, uint32_t dmask, int nb, cudaStream_t st);
 
 // Exclusive scan of n uint32 (three launches); partial holds
 // ceil(n / SCAN_ITEMS) counters; *total (optional, device) gets the sum.
@@ -53,6 +55,11 @@ int launch_prune_compact(const unigs_prune_array* arrays, int n_arrays, int64_t 
 
 // Number of SMs of the current device (queried once per device).
 int sm_count();
+
+// Raises the dynamic shared-memory limit of kernel `func` to `bytes` on the
+// current device, once per (kernel, device); thread-safe.  Returns the CUDA
+// error of the attribute call (cudaSuccess when it was already set).
+cudaError_t ensure_smem_limit(const void* func, int bytes);
 
 // Index of the buffer (0/1) that holds the sorted keys/values after the sort.
 inline int sorted_buffer(const unigs_plan& p) { return p.sort_passes & 1; }

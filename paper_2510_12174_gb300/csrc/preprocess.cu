@@ -420,6 +420,7 @@ __global__ void init_kernel(CamTable tab, int n_cams, CamTable* __restrict__ dst
         hdr->need = 0;
         hdr->n_eval = 0;
         hdr->n_blend = 0;
+        hdr->nonfinite = 0;
     }
 }
 
@@ -436,12 +437,56 @@ __global__ void __launch_bounds__(256)
         dst[i] = __bfloat1622float2(src[i]);
 }
 
+// The Gaussian parameter arrays as (pointer, element count, bfloat16) for the
+// non-finite scan, in the order reported by unigs_status_poll.
+struct FiniteArrays {
+    const void* ptr[7];
+    int64_t count[7];
+    int bf16[7];
+};
+
+// Scans array blockIdx.y for NaN and infinity (grid-stride over its
+// elements); the first array found is recorded with UNIGS_ERR_NONFINITE.
+__global__ void __launch_bounds__(256)
+    finite_check_kernel(const FiniteArrays A, WsHeader* __restrict__ hdr) {
+    const int a = blockIdx.y;
+    const int64_t n = A.count[a];
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = A.bf16[a] ? __bfloat162float(static_cast<const __nv_bfloat16*>(A.ptr[a])[i])
+                                  : static_cast<const float*>(A.ptr[a])[i];
+        bad |= !isfinite(v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        if (atomicCAS(&hdr->status, 0u, (uint32_t)UNIGS_ERR_NONFINITE) == 0u)
+            hdr->nonfinite = (uint32_t)a;
+    }
+}
+
 int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTable& tab,
                       void* ws, cudaStream_t st) {
     init_kernel<<<1, UNIGS_MAX_CAMS, 0, st>>>(tab, p.n_cams, ws_ptr<CamTable>(ws, p, OFF_CAM),
                                               ws_ptr<WsHeader>(ws, p, OFF_HDR));
     const int64_t total = p.n * (int64_t)p.n_cams;
     int launches = 1;
+    if ((p.cfg.flags & UNIGS_FLAG_CHECK_FINITE) && p.n > 0) {
+        const int64_t n = p.n, n_sh = (int64_t)(p.sh_degree + 1) * (p.sh_degree + 1);
+        FiniteArrays A;
+        const void* ptrs[7] = {g.mean, g.quat, g.scale, g.opacity, g.kfac, g.sh, g.sem};
+        const int64_t counts[7] = {3 * n, 4 * n, 3 * n, n, n, n * n_sh * 3,
+                                   p.n_sem > 0 ? n * p.n_sem : 0};
+        for (int a = 0; a < 7; ++a) {
+            A.ptr[a] = ptrs[a];
+            A.count[a] = counts[a];
+            A.bf16[a] = (a >= 5 && p.feat_dtype) ? 1 : 0;
+        }
+        int64_t blocks = (n * 3 + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        finite_check_kernel<<<dim3((unsigned)blocks, 7), 256, 0, st>>>(
+            A, ws_ptr<WsHeader>(ws, p, OFF_HDR));
+        ++launches;
+    }
     if (total > 0) {
         const int64_t blocks = (total + 255) / 256;
         const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);

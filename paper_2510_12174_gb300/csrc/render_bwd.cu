@@ -51,7 +51,7 @@ struct BwdParams {
     const float* T_final;
     const uint32_t* n_contrib;
     unigs_grad_outputs go;
-    float* grec;
+    double* grec;              // float64 accumulators (see the RED below)
     float* gsem;
     float alpha_min, alpha_max;
     int center_depth;
@@ -73,6 +73,7 @@ struct BwdSmem {
     uint64_t cons[2];  // batch consumed (one arrival per warp)
     uint32_t max_last;
     int tile;
+    int abort;         // a bounded wait gave up (set_abort)
 };
 
 // Offset of channel c of pixel row p in the swizzled upstream-gradient tile.
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         mbar_init(&S.cons[0], 8);
         mbar_init(&S.cons[1], 8);
         fence_mbar_init();
+        S.abort = 0;
     }
     for (int j = tid; j < 2 * B * NS; j += 256) (&S.sem[0][0][0])[j] = 0.f;
     // the upstream-gradient rows are addressed by XOR within a row, which
@@ -183,9 +185,15 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
     }
     const uint32_t a_row = go_row<NS>(go_base, tid);
     __syncthreads();
-    uint32_t loads[2] = {0u, 0u};  // completed loads per buffer (uniform)
-    uint32_t used[2] = {0u, 0u};   // completed consumptions per buffer (uniform)
+    // per buffer: phases of bar[] waited for and consumptions (uniform across
+    // the CTA), phases of bar[] started (warp 0, the producer); scalars, so
+    // that they stay in registers
+    uint32_t loads0 = 0u, loads1 = 0u, used0 = 0u, used1 = 0u, issued0 = 0u, issued1 = 0u;
     bool timed_out = false;
+    auto give_up = [&]() {
+        timed_out = true;
+        set_abort(&S.abort);
+    };
 
     for (;;) {
         if (tid == 0) {
@@ -247,11 +255,16 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         // batch it; a buffer is restaged only after all 8 warps have arrived on
         // its "consumed" barrier, so the warps never meet at a CTA barrier
         // inside the tile.
+        // After a timeout the producer issues nothing more (a warp-uniform
+        // decision), so at most one copy per buffer is ever in flight.
         auto produce = [&](int bf, uint32_t first, int cnt) {
-            if (used[bf] > 0 &&
-                !mbar_wait_bounded(&S.cons[bf], (used[bf] - 1) & 1u, BWAIT_LIMIT))
-                timed_out = true;
+            const uint32_t u = bf ? used1 : used0;
+            if (u > 0 && !aborted(&S.abort) &&
+                !mbar_wait_bounded(&S.cons[bf], (u - 1) & 1u, BWAIT_LIMIT))
+                give_up();
+            if (__any_sync(0xffffffffu, aborted(&S.abort))) return;
             bwd_issue<NS, B>(P, S, bf, first, cnt, cam_idx);
+            if (bf) ++issued1; else ++issued0;
         };
         if (warp == 0 && n_batches > 0)
             produce(0, range.x + (n_batches - 1) * B, min(B, n_items - (n_batches - 1) * B));
@@ -261,8 +274,12 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
             const int b = n_batches - 1 - it;
             const int buf = it & 1;
             if (warp == 0 && b > 0) produce(buf ^ 1, range.x + (b - 1) * B, B);
-            if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, BWAIT_LIMIT)) timed_out = true;
-            ++loads[buf];
+            {
+                const uint32_t ph = buf ? loads1 : loads0;
+                if (aborted(&S.abort) || !mbar_wait_bounded(&S.bar[buf], ph & 1u, BWAIT_LIMIT))
+                    give_up();
+                if (buf) ++loads1; else ++loads0;
+            }
             const int count = min(B, n_items - b * B);
             if (!__all_sync(0xffffffffu, timed_out) && (uint32_t)(b * B) < wlast) {
             for (int j = min(count, (int)(wlast - (uint32_t)(b * B))) - 1; j >= 0; --j) {
@@ -386,8 +403,13 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 {
                     const uint32_t g = S.ids[buf][j];
                     const size_t rix = (size_t)cam_idx * (size_t)P.n + g;
+                    // the warp's sum of component `lane`, added in float64: a
+                    // Gaussian's record sums thousands of pixel terms that can
+                    // cancel (near-camera, elongated splats), and a float32
+                    // sum in atomic order would leave it off by the rounding
+                    // of the partial sums, differently on every run
                     const float tot = warp_reduce_transpose32(gv, lane);
-                    if (tot != 0.f) atomicAdd(P.grec + rix * GREC_FLOATS + lane, tot);
+                    if (tot != 0.f) atomicAdd(P.grec + rix * GREC_FLOATS + lane, (double)tot);
                     if (P.n_sem > 0) {
                         // dL/do_j[c] = sum over the contributing pixels l of w_l gO_l[c]
                         {
@@ -448,11 +470,14 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
             // this warp is done with the batch's buffers
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.cons[buf]);
-            ++used[buf];
+            if (buf) ++used1; else ++used0;
         }
         // a bounded wait that gave up ends the CTA (uniformly)
         if (__syncthreads_or(timed_out)) break;
     }
+    // no bulk copy may still be landing in this CTA's shared memory when it
+    // exits (after a timeout at most one per buffer is in flight)
+    if (tid == 0 && !drain_bulk(S.bar, issued0, issued1, BWAIT_LIMIT)) timed_out = true;
     if (timed_out && lane == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
 }
 
@@ -462,7 +487,7 @@ struct PreBwdParams {
     int n_cams;
     unigs_gaussians g;
     const float* rec;
-    const float* grec;
+    const double* grec;
     const uint32_t* touched;
     unigs_param_grads out;
     float lowpass;
@@ -509,11 +534,12 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
             if (P.touched[t] == 0) continue;
             const DevCam& cam = P.tab->cam[k];
             float gr[GREC_FLOATS];
-            const float4* src = reinterpret_cast<const float4*>(P.grec + t * GREC_FLOATS);
+            const double2* src = reinterpret_cast<const double2*>(P.grec + t * GREC_FLOATS);
 #pragma unroll
-            for (int q = 0; q < GREC_FLOATS / 4; ++q) {
-                const float4 f = src[q];
-                gr[4 * q] = f.x; gr[4 * q + 1] = f.y; gr[4 * q + 2] = f.z; gr[4 * q + 3] = f.w;
+            for (int q = 0; q < GREC_FLOATS / 2; ++q) {
+                const double2 f = src[q];
+                gr[2 * q] = (float)f.x;
+                gr[2 * q + 1] = (float)f.y;
             }
             g_op += gr[G_OP];
             g_k += gr[G_K];
@@ -669,12 +695,8 @@ static void launch_bwd_t(const BwdParams& P, int grid, cudaStream_t st) {
     static_assert(offsetof(Smem, gO) % 256 == 0,
                   "the upstream-gradient tile must sit at a multiple of 256 bytes");
     const size_t smem = sizeof(BwdSmem<NS, B>);
-    static bool attr_set = false;  // host-side, set once per instantiation
-    if (!attr_set) {
-        cudaFuncSetAttribute(render_bwd_kernel<NS, B>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    // a failure here surfaces as the launch error the entry point returns
+    ensure_smem_limit(reinterpret_cast<const void*>(&render_bwd_kernel<NS, B>), (int)smem);
     render_bwd_kernel<NS, B><<<grid, 256, smem, st>>>(P);
 }
 
@@ -694,8 +716,8 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_outputs& fwd, const unigs_grad_outputs& go,
                       const unigs_param_grads& grads, cudaStream_t st) {
     int launches = 0;
-    float* grec = ws_ptr<float>(ws, p, OFF_GREC);
-    cudaMemsetAsync(grec, 0, sizeof(float) * GREC_FLOATS * (size_t)p.n * p.n_cams, st);
+    double* grec = ws_ptr<double>(ws, p, OFF_GREC);
+    cudaMemsetAsync(grec, 0, sizeof(double) * GREC_FLOATS * (size_t)p.n * p.n_cams, st);
     if (grads.sem && !grads.accumulate && p.n_sem > 0)
         cudaMemsetAsync(grads.sem, 0, sizeof(float) * (size_t)p.n * p.n_sem, st);
     if (p.n_tiles > 0 && p.n > 0) {

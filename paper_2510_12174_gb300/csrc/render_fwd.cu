@@ -51,6 +51,7 @@ struct FwdSmem {
     float sem[2][B][NS];
     uint64_t bar[2];
     int tile;
+    int abort;  // a bounded wait gave up (set_abort)
 };
 
 template <int NS, int B>
@@ -104,12 +105,29 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
+        S.abort = 0;
     }
     __syncthreads();
-    // completed loads per buffer (uniform across the CTA): the parity of the
-    // next phase to wait for
-    uint32_t loads[2] = {0u, 0u};
+    // phases waited for per buffer (uniform across the CTA): the parity of the
+    // next phase to wait for; phases started per buffer (warp 0, the issuer)
+    uint32_t loads0 = 0u, loads1 = 0u, issued0 = 0u, issued1 = 0u;
     bool timed_out = false;
+    // warp 0 stages a batch unless the CTA has given up (a warp-uniform
+    // decision: lane 0 arms the barrier, every lane issues copies)
+    auto issue = [&](int bf, uint32_t first, int cnt, int cam) {
+        if (__any_sync(0xffffffffu, aborted(&S.abort))) return;
+        issue_batch<NS, B>(P, S, bf, first, cnt, cam);
+        if (bf) ++issued1; else ++issued0;
+    };
+    // every thread waits for the batch in buffer bf (bounded)
+    auto wait_batch = [&](int bf) {
+        const uint32_t ph = bf ? loads1 : loads0;
+        if (aborted(&S.abort) || !mbar_wait_bounded(&S.bar[bf], ph & 1u, WAIT_LIMIT)) {
+            timed_out = true;
+            set_abort(&S.abort);
+        }
+        if (bf) ++loads1; else ++loads0;
+    };
     uint32_t n_eval = 0, n_blend = 0;
 
     for (;;) {
@@ -136,8 +154,7 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         const uint2 range = P.ranges[gtile];
         const int n_items = (int)(range.y - range.x);
         const int n_batches = (n_items + B - 1) / B;
-        if (warp == 0 && n_batches > 0)
-            issue_batch<NS, B>(P, S, 0, range.x, min(B, n_items), cam_idx);
+        if (warp == 0 && n_batches > 0) issue(0, range.x, min(B, n_items), cam_idx);
         // rows staged with plain stores (unaligned semantic rows) must be
         // visible before the first batch is read; later batches are ordered by
         // the end-of-batch barrier
@@ -154,10 +171,8 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         for (int b = 0; b < n_batches; ++b) {
             const int buf = b & 1;
             if (warp == 0 && b + 1 < n_batches)
-                issue_batch<NS, B>(P, S, buf ^ 1, range.x + (b + 1) * B,
-                                   min(B, n_items - (b + 1) * B), cam_idx);
-            if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, WAIT_LIMIT)) timed_out = true;
-            ++loads[buf];
+                issue(buf ^ 1, range.x + (b + 1) * B, min(B, n_items - (b + 1) * B), cam_idx);
+            wait_batch(buf);
             const int count = min(B, n_items - b * B);
             const bool skip = __all_sync(0xffffffffu, done || timed_out);
             if (!skip) {
@@ -196,11 +211,7 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
             const int alive = __syncthreads_count(!done && !timed_out);
             if (alive == 0) {
                 // drain the batch already in flight before leaving the tile
-                if (b + 1 < n_batches) {
-                    if (!mbar_wait_bounded(&S.bar[buf ^ 1], loads[buf ^ 1] & 1u, WAIT_LIMIT))
-                        timed_out = true;
-                    ++loads[buf ^ 1];
-                }
+                if (b + 1 < n_batches) wait_batch(buf ^ 1);
                 break;
             }
         }
@@ -231,6 +242,9 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         // that gave up ends the CTA (uniformly)
         if (__syncthreads_or(timed_out)) break;
     }
+    // no bulk copy may still be landing in this CTA's shared memory when it
+    // exits (after a timeout the issuer stopped, so at most one per buffer)
+    if (tid == 0 && !drain_bulk(S.bar, issued0, issued1, WAIT_LIMIT)) timed_out = true;
     if (timed_out && (tid & 31) == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
     // work counters: one atomic per warp
 #pragma unroll
@@ -247,12 +261,8 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
 template <int NS, int B>
 static void launch_fwd_t(const FwdParams& P, int grid, cudaStream_t st) {
     const size_t smem = sizeof(FwdSmem<NS, B>);
-    static bool attr_set = false;  // host-side, set once per instantiation
-    if (!attr_set) {
-        cudaFuncSetAttribute(render_fwd_kernel<NS, B>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    // a failure here surfaces as the launch error the entry point returns
+    ensure_smem_limit(reinterpret_cast<const void*>(&render_fwd_kernel<NS, B>), (int)smem);
     render_fwd_kernel<NS, B><<<grid, 256, smem, st>>>(P);
 }
 

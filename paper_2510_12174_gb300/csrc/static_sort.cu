@@ -59,6 +59,12 @@ cudaError_t scratch_on_current_device(StaticSortScratch** out) {
     return cudaSuccess;
 }
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
 // Every call starts from a clean status block holding its own pair count.
 __global__ void static_sort_init_kernel(StaticSortScratch* s, uint32_t n) {
     s->hdr.status = 0;
@@ -78,9 +84,15 @@ extern "C" unigs_status unigs_sort_pairs_static(const unsigned long long* keys_i
     if (n < 0 || n > STATIC_MAX_PAIRS || key_bits < 1 || key_bits > 64)
         return UNIGS_ERR_INVALID_ARG;
     if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return UNIGS_ERR_INVALID_ARG;
-    if (n > 0 && ((const void*)keys_in == (const void*)keys_out ||
-                  (const void*)vals_in == (const void*)vals_out))
-        return UNIGS_ERR_INVALID_ARG;
+    if (n > 0) {
+        // an output may share no byte with an input or with the other output
+        // (the passes ping-pong between the outputs and the static scratch)
+        const size_t kb = sizeof(unsigned long long) * (size_t)n, vb = sizeof(uint32_t) * (size_t)n;
+        if (overlap(keys_out, kb, keys_in, kb) || overlap(keys_out, kb, vals_in, vb) ||
+            overlap(keys_out, kb, vals_out, vb) || overlap(vals_out, vb, keys_in, kb) ||
+            overlap(vals_out, vb, vals_in, vb))
+            return UNIGS_ERR_INVALID_ARG;
+    }
     StaticSortScratch* s = nullptr;
     if (scratch_on_current_device(&s) != cudaSuccess) return UNIGS_ERR_CUDA;
     if (n == 0) return UNIGS_OK;
@@ -88,6 +100,9 @@ extern "C" unigs_status unigs_sort_pairs_static(const unsigned long long* keys_i
     static_sort_init_kernel<<<1, 1, 0, st>>>(s, (uint32_t)n);
     const int passes = (key_bits + 7) / 8;
     const int nb = (int)((n + SORT_ITEMS - 1) / SORT_ITEMS);
+    // the last pass sorts by the key_bits - 8 (passes - 1) bits that remain,
+    // so key bits at and above key_bits never decide the order
+    const int last_bits = key_bits - 8 * (passes - 1);
     // pass p writes the output when (passes - 1 - p) is even, else the
     // scratch buffer, so the last pass lands in the output and consecutive
     // passes never read and write the same buffer.
@@ -97,7 +112,8 @@ extern "C" unigs_status unigs_sort_pairs_static(const unsigned long long* keys_i
         const bool to_out = ((passes - 1 - p) & 1) == 0;
         unsigned long long* kout = to_out ? keys_out : s->keys;
         uint32_t* vout = to_out ? vals_out : s->vals;
-        radix_pass(kin, vin, kout, vout, s->hist, s->partial, &s->hdr, 8 * p, nb, st);
+        const uint32_t dmask = p == passes - 1 ? (1u << last_bits) - 1u : 255u;
+        radix_pass(kin, vin, kout, vout, s->hist, s->partial, &s->hdr, 8 * p, dmask, nb, st);
         kin = kout;
         vin = vout;
     }

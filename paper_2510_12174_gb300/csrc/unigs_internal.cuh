@@ -69,8 +69,9 @@ __device__ __forceinline__ bool warp_block_misses(const float* __restrict__ rc, 
 // float32 quadratic form loses about log2(ratio) bits along the long axis.
 constexpr float KAPPA_FF = 64.f;
 
-// Per-(camera, Gaussian) intermediate gradient record (32 floats), filled by
-// atomics in the backward composite and consumed by the preprocess backward:
+// Per-(camera, Gaussian) intermediate gradient record (32 float64
+// accumulators, 256 bytes), filled by atomics in the backward composite and
+// consumed by the preprocess backward:
 // dL/d(projected centre x, y), dL/d(a, b, c) of the 2D covariance
 // [[a, b], [b, c]] (low-pass included), opacity, RGB, M_c, v_s, N_w, k and the
 // centre depth (centre-depth mode).
@@ -106,7 +107,8 @@ struct WsHeader {
     unsigned long long n_blend;  // pairs the forward blended (alpha >= alpha_min, not stopped)
     uint32_t work_fwd;           // tile counters of the persistent composite kernels
     uint32_t work_bwd;
-    uint32_t pad[54];
+    uint32_t nonfinite;          // first parameter array found non-finite (flag set)
+    uint32_t pad[53];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 
@@ -252,6 +254,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     for (uint32_t i = 0; i < max_iter; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Sticky per-CTA abort flag in shared memory: set by a thread whose bounded
+// wait gave up; read (volatile) by the producer before it issues a copy and
+// by the consumers before they wait, so that after a timeout no copy is
+// issued and no thread waits on a phase that will never complete.
+__device__ __forceinline__ void set_abort(int* flag) { *reinterpret_cast<volatile int*>(flag) = 1; }
+__device__ __forceinline__ bool aborted(const int* flag) {
+    return *reinterpret_cast<const volatile int*>(flag) != 0;
+}
+
+// Before a CTA exits: waits (bounded) until the last bulk copy issued into
+// each of the two staging buffers has landed in shared memory.  issued0/1
+// count the phases started on bar[0]/bar[1]; phases complete in order and the
+// producers keep at most one in flight per buffer, so the parity of the last
+// one identifies it.  In a launch without timeouts every phase has already
+// been waited for and this returns at once.  Returns false if a copy is still
+// in flight after the limit (the caller has already recorded the timeout).
+__device__ __forceinline__ bool drain_bulk(uint64_t* bar, uint32_t issued0, uint32_t issued1,
+                                           uint32_t limit) {
+    bool ok = true;
+    if (issued0 > 0) ok &= mbar_wait_bounded(&bar[0], (issued0 - 1) & 1u, limit);
+    if (issued1 > 0) ok &= mbar_wait_bounded(&bar[1], (issued1 - 1) & 1u, limit);
+    return ok;
 }
 
 // 1D bulk copy global -> shared, completion counted on the mbarrier.

@@ -77,35 +77,80 @@ def forward_errors(r, out, ref_outs, n_sem):
     return errs
 
 
-def grad_errors(got, ref, rel_floor=1e-2):
-    """Per parameter type: (max, 99.9th percentile) of
-    |g - g_ref| / max(|g_ref|, rel_floor * RMS), the max of the same with a
-    0.1 * RMS floor, the vector-norm relative error, and the RMS."""
+# Gradient floor: an element is compared relative to max(|g_ref|, FLOOR * RMS of
+# its parameter type).  Each (pixel, Gaussian) term of a per-Gaussian gradient
+# is formed in float32 (alpha recomputation, transmittance restoration along
+# the list, the ray-ellipsoid chain, approximate reciprocals), so a sum whose
+# terms cancel - the rotation gradient of a nearly isotropic Gaussian, the
+# centre gradient of a near-camera splat over thousands of pixels - keeps an
+# absolute error of a few float32 roundings of its largest terms.  Measured on
+# the test scenes: up to 8e-5 RMS on such elements (deterministic: the same
+# for every launch shape, and the per-Gaussian sums are accumulated in
+# float64), against up to 7e-4 RMS for a plain float32 evaluation of the
+# oracle's own definition.  Hence every element is held to 1e-3 relative
+# above 0.1 RMS and 1e-4 RMS absolute below it.
+GRAD_FLOOR = 1e-1
+# The floor of the scope's criterion, held on all but STRICT_FRACTION of the
+# elements.
+STRICT_FLOOR = 1e-3
+STRICT_FRACTION = 1e-3
+
+
+def grad_errors(got, ref):
+    """Per parameter type: the max of |g - g_ref| / max(|g_ref|, f RMS) for
+    f = GRAD_FLOOR and for f = STRICT_FLOOR, the fraction of elements above
+    1e-3 with the strict floor, the vector-norm relative error and the RMS."""
     res = {}
     for k, g_ref in ref.items():
-        g = got[k].float().cpu().numpy().reshape(g_ref.shape)
+        g = got[k].float().cpu().numpy().reshape(g_ref.shape).astype(np.float64)
         rms = float(np.sqrt(np.mean(g_ref ** 2))) if g_ref.size else 0.0
-        den = np.maximum(np.abs(g_ref), rel_floor * rms + 1e-30)
-        e = np.abs(g - g_ref) / den
-        e10 = np.abs(g - g_ref) / np.maximum(np.abs(g_ref), 0.1 * rms + 1e-30)
+        d = np.abs(g - g_ref)
+        e = d / np.maximum(np.abs(g_ref), GRAD_FLOOR * rms + 1e-30)
+        es = d / np.maximum(np.abs(g_ref), STRICT_FLOOR * rms + 1e-30)
         nrm = float(np.linalg.norm(g - g_ref) / max(np.linalg.norm(g_ref), 1e-30))
         res[k] = dict(max=float(e.max()) if e.size else 0.0,
-                      p999=float(np.quantile(e, 0.999)) if e.size else 0.0,
-                      max_floor01=float(e10.max()) if e.size else 0.0, norm=nrm, rms=rms)
+                      max_strict=float(es.max()) if es.size else 0.0,
+                      frac_strict=float((es > 1e-3).mean()) if es.size else 0.0,
+                      norm=nrm, rms=rms)
     return res
 
 
-def check_grad_errors(e, p999=1e-3, max_floor01=1e-2, norm=1e-4):
-    """Gradient criterion.  Per-Gaussian gradients are float32 sums over pixels
-    whose terms can cancel (e.g. the rotation gradient of a nearly isotropic
-    Gaussian), so the element-wise bound uses a floor proportional to the RMS
-    of that parameter type: 99.9% of elements within p999 of max(|g|, 1e-2 RMS),
-    every element within max_floor01 of max(|g|, 0.1 RMS), and the whole
-    vector within ``norm`` relative error."""
+def check_grad_errors(e, tol=1e-3, norm=1e-4):
+    """Gradient criterion, every element of every parameter type:
+    |g - g_ref| <= tol * max(|g_ref|, GRAD_FLOOR * RMS); at most a fraction
+    STRICT_FRACTION of the elements above tol * max(|g_ref|, STRICT_FLOOR *
+    RMS); and the whole vector within ``norm`` relative error."""
     for k, d in e.items():
-        print(f"grad {k}: p99.9 {d['p999']:.2e} max {d['max']:.2e} max(0.1rms) "
-              f"{d['max_floor01']:.2e} norm {d['norm']:.2e} rms {d['rms']:.3e}")
+        print(f"grad {k}: max {d['max']:.2e} (floor {GRAD_FLOOR:g} rms) max {d['max_strict']:.2e} "
+              f"(floor {STRICT_FLOOR:g} rms, {d['frac_strict']:.1e} above) norm {d['norm']:.2e} "
+              f"rms {d['rms']:.3e}")
     for k, d in e.items():
-        assert d["p999"] < p999, (k, d)
-        assert d["max_floor01"] < max_floor01, (k, d)
+        assert d["max"] < tol, (k, d)
+        assert d["frac_strict"] <= STRICT_FRACTION, (k, d)
         assert d["norm"] < norm, (k, d)
+
+
+# Fraction of pixels whose float64 discrete decisions fall inside the
+# ambiguity bands (the kernels' own float32 error bounds, oracle.raster.Bands):
+# the forward compares every other pixel element-wise; the gradient tests zero
+# the upstream gradient there.
+MAX_AMBIGUOUS_FWD = 2e-3
+MAX_AMBIGUOUS_GRAD = 4e-2
+
+
+def sampled_errors(got, ref):
+    """Forward errors at sampled pixels.  ``got``/``ref`` map a channel name to
+    [n_samples, C] arrays; rgb, normal_g and kmap are absolute, depth and
+    logits relative to max(|ref|, RMS of that channel over the samples)."""
+    e = {}
+    for k in got:
+        g, x = np.asarray(got[k], np.float64), np.asarray(ref[k], np.float64)
+        if not len(x):
+            e[k] = 0.0
+            continue
+        if k in ("depth", "logits"):
+            rms = np.sqrt(np.mean(x ** 2, axis=0, keepdims=True))
+            e[k] = float((np.abs(g - x) / np.maximum(np.abs(x), np.maximum(rms, 1e-30))).max())
+        else:
+            e[k] = float(np.abs(g - x).max())
+    return e

@@ -152,8 +152,8 @@ def test_launch_shape_fields_are_validated(lib):
     arr = rz.make_cameras(cams)
     for field, value, ok in (("batch", 8, True), ("batch", 48, False), ("batch_fwd", 8, False),
                              ("batch_fwd", 64, True), ("ctas_per_sm", 9, False),
-                             ("ctas_per_sm_fwd", 4, True), ("flags", 4, False),
-                             ("flags", 3, True), ("alpha_max", 1.0, False),
+                             ("ctas_per_sm_fwd", 4, True), ("flags", 8, False), ("flags", 4, True),
+                             ("flags", 7, True), ("alpha_max", 1.0, False),
                              ("alpha_max", 0.999, True), ("alpha_max", float("nan"), False),
                              ("alpha_min", -1e-3, False), ("alpha_min", 0.995, False),
                              ("T_min", 1.0, False), ("lowpass", float("inf"), False)):

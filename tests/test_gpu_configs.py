@@ -22,8 +22,9 @@ from paper_2510_12174_gb300 import abi
 from paper_2510_12174_gb300 import rasterizer as rz
 from paper_2510_12174_gb300 import scenes
 
-from gpu_helpers import (TOL_ABS, TOL_REL, check_grad_errors, flat_upstream, forward_errors,
-                         grad_errors, masked_upstream)
+from gpu_helpers import (MAX_AMBIGUOUS_FWD, MAX_AMBIGUOUS_GRAD, TOL_ABS, TOL_REL,
+                         check_grad_errors, flat_upstream, forward_errors, grad_errors,
+                         masked_upstream, sampled_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +53,7 @@ def test_config1_forward_every_pixel():
     _, ref, _ = oracle.render(sc, cams, binning=ref_b, with_normal_d=False)
     e = forward_errors(r, out, ref, sc.n_sem)
     print("config1", e)
-    assert e["ambiguous_fraction"] < 0.03 and e["n_contrib"] == 0
+    assert e["ambiguous_fraction"] < MAX_AMBIGUOUS_FWD and e["n_contrib"] == 0
     assert e["rgb"] < TOL_ABS and e["normal_g"] < TOL_ABS and e["kmap"] < TOL_ABS
     assert e["T_final"] < TOL_ABS
     assert e["depth"] < TOL_REL and e["logits"] < TOL_REL
@@ -90,11 +91,12 @@ def test_config2_band_forward_and_gradients():
     _, ref, _ = oracle.render(sc, cams, binning=ref_b, tiles=[band], with_normal_d=False)
     e, n_amb = _band_errors(r, out, ref[0], mask, sc.n_sem)
     print("config2 band", e, "ambiguous", n_amb)
-    assert n_amb < 0.03 * mask.sum()
+    assert n_amb < MAX_AMBIGUOUS_FWD * mask.sum()
     assert e["rgb"] < TOL_ABS and e["normal_g"] < TOL_ABS and e["kmap"] < TOL_ABS
     assert e["T_final"] < TOL_ABS and e["depth"] < TOL_REL and e["logits"] < TOL_REL
     # gradients of a loss on the band only
     up = scenes.upstream_grads(cams, sc.n_sem, seed=41)
+    assert ref[0]["amb_grad"].numpy()[mask].mean() < MAX_AMBIGUOUS_GRAD
     drop = ~mask | ref[0]["amb_grad"].numpy()
     up = masked_upstream(up, [drop])
     up["normal_d"] = [np.zeros_like(x) for x in up["normal_d"]]
@@ -137,7 +139,10 @@ def test_config4_batched_mixed_resolution():
         TX = (cam.width + 15) // 16
         views = {key: r.split(out[key], ch)[k].cpu().numpy() for key, ch in
                  (("rgb", 3), ("depth", 1), ("normal_g", 3), ("kmap", 1), ("logits", 64))}
-        worst = {key: 0.0 for key in views}
+        okey = {"rgb": "rgb", "depth": "depth", "normal_g": "normal", "kmap": "kmap",
+                "logits": "logits"}
+        got = {key: [] for key in views}
+        exp = {key: [] for key in views}
         n_amb = 0
         for _ in range(40):
             u, v = int(rng.integers(0, cam.width)), int(rng.integers(0, cam.height))
@@ -150,19 +155,15 @@ def test_config4_batched_mixed_resolution():
             if bool(rr["amb_fwd"][0]):
                 n_amb += 1
                 continue
-            for key, okey in (("rgb", "rgb"), ("normal_g", "normal"), ("kmap", "kmap")):
-                worst[key] = max(worst[key], float(np.abs(views[key][..., v, u]
-                                                          - rr[okey][0].numpy()).max()))
-            d = rr["depth"][0].item()
-            worst["depth"] = max(worst["depth"], abs(views["depth"][v, u] - d) / max(abs(d), 1.0))
-            lg = rr["logits"][0].numpy()
-            worst["logits"] = max(worst["logits"], float(
-                np.abs(views["logits"][:, v, u] - lg).max() / max(np.sqrt(np.mean(lg ** 2)), 1e-3)))
+            for key in views:
+                got[key].append(np.atleast_1d(views[key][..., v, u]))
+                exp[key].append(np.atleast_1d(rr[okey[key]][0].numpy()))
+        worst = sampled_errors(got, exp)
         print("config4", (w, h), worst, "ambiguous", n_amb)
-        assert n_amb < 6
+        assert n_amb <= 2
         assert worst["rgb"] < TOL_ABS and worst["normal_g"] < TOL_ABS
         assert worst["kmap"] < TOL_ABS and worst["depth"] < TOL_REL
-        assert worst["logits"] < 10 * TOL_REL
+        assert worst["logits"] < TOL_REL
 
 
 def test_config5_loss_at_full_size():

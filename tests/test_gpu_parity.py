@@ -2,8 +2,9 @@
 
 Binning (keys, values, ranges) must match bit for bit; the forward within the
 stated tolerances on every pixel whose float64 discrete decisions are not
-within a narrow band of a threshold (those are counted and must stay rare);
-gradients within 1e-3 relative of the oracle's exact derivative.
+within the kernels' float32 error bound of a threshold (those are counted and
+must stay below 0.2% of the pixels); gradients within 1e-3 relative of the
+oracle's exact derivative (gpu_helpers.check_grad_errors).
 """
 import numpy as np
 import pytest
@@ -15,8 +16,9 @@ from paper_2510_12174_gb300 import abi
 from paper_2510_12174_gb300 import rasterizer as rz
 from paper_2510_12174_gb300 import scenes
 
-from gpu_helpers import (TOL_ABS, TOL_REL, check_grad_errors, dilate, flat_upstream,
-                         forward_errors, grad_errors, masked_upstream)
+from gpu_helpers import (MAX_AMBIGUOUS_FWD, MAX_AMBIGUOUS_GRAD, TOL_ABS, TOL_REL,
+                         check_grad_errors, dilate, flat_upstream, forward_errors, grad_errors,
+                         masked_upstream, sampled_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +65,7 @@ def test_forward_parity(case):
     _, ref, _ = oracle.render(sc, cams, with_normal_d=False)
     e = forward_errors(r, out, ref, sc.n_sem)
     print(case, e)
-    assert e["ambiguous_fraction"] < 0.03
+    assert e["ambiguous_fraction"] < MAX_AMBIGUOUS_FWD
     assert e["rgb"] < TOL_ABS and e["normal_g"] < TOL_ABS and e["kmap"] < TOL_ABS
     assert e["T_final"] < TOL_ABS
     assert e["depth"] < TOL_REL and e["logits"] < TOL_REL
@@ -150,9 +152,14 @@ def test_depth_normal_stage():
     assert rel.max() < 1e-3
 
 
-def _grad_case(sc, cams, with_nd=False, seed=21):
+def _oracle_case(sc, cams, with_nd=False, seed=21):
+    """Upstream gradients zeroed on the ambiguous pixels (dilated by the
+    stencil reach of Alg. 3 when the normal-from-depth term is included) and
+    the oracle's exact parameter gradients of L = sum <output, upstream>."""
     up = scenes.upstream_grads(cams, sc.n_sem, seed=seed)
     _, ref_fwd, _ = oracle.render(sc, cams)
+    amb = np.mean(np.concatenate([rf["amb_grad"].numpy().ravel() for rf in ref_fwd]))
+    assert amb < MAX_AMBIGUOUS_GRAD, amb
     masks = []
     for k, rf in enumerate(ref_fwd):
         m = rf["amb_grad"].numpy()
@@ -167,6 +174,11 @@ def _grad_case(sc, cams, with_nd=False, seed=21):
             bad = dilate(rf["nd_amb"].numpy() | masks[k], 2)
             up["normal_d"][k][:, bad] = 0
     _, gref, _ = oracle.render_and_grad(sc, cams, up)
+    return up, gref
+
+
+def _grad_case(sc, cams, with_nd=False, seed=21):
+    up, gref = _oracle_case(sc, cams, with_nd, seed)
     r = rz.Renderer(rz.DeviceScene.from_scene(sc), cams)
     out = r.forward()
     fu = flat_upstream(up)
@@ -187,11 +199,11 @@ def test_backward_parity(n_sem):
 
 def test_backward_parity_two_cameras_with_depth_normal():
     """Includes Alg. 3: the depth gradient then carries the normal-from-depth
-    term, whose float32 error grows with f/step (see the A6 note), so the
-    element-wise bound is 3x looser."""
+    term, which differentiates a finite difference of the depth and so scales
+    the float32 error of each pair's depth by about f / (2 step): the
+    element-wise bound is 3e-3 instead of 1e-3."""
     sc, cams = scenes.small_room(n=5000, width=60, height=44, n_sem=16, seed=13, n_cams=2)
-    check_grad_errors(_grad_case(sc, cams, with_nd=True), p999=3e-3, max_floor01=3e-2,
-                      norm=3e-4)
+    check_grad_errors(_grad_case(sc, cams, with_nd=True), tol=3e-3, norm=3e-4)
 
 
 def test_backward_parity_bf16_features():
@@ -243,23 +255,30 @@ def test_empty_and_culled_inputs():
     assert torch.all(out["n_contrib"] == 0)
 
 
-def test_autograd_function_matches_direct_backward():
-    sc, cams = scenes.small_room(n=3000, width=48, height=40, n_sem=8, seed=16)
+def test_autograd_function_matches_oracle_and_direct_backward():
+    """rasterizer.render (the torch.autograd.Function around the forward and
+    backward entry points, normal-from-depth included) against the oracle's
+    exact gradients, and against the direct backward call (which differs only
+    in the order of the float32 atomic additions)."""
+    sc, cams = scenes.small_room(n=3000, width=48, height=40, n_sem=8, seed=16, n_cams=2)
+    up, gref = _oracle_case(sc, cams, with_nd=True, seed=2)
     ds = rz.DeviceScene.from_scene(sc)
     for t in ds.tensors():
         t.requires_grad_(True)
     r = rz.Renderer(ds, cams)
     outs = rz.render(r)
-    up = flat_upstream(scenes.upstream_grads(cams, sc.n_sem, seed=2))
-    loss = sum((o * up[k]).sum() for o, k in zip(outs, ("rgb", "depth", "normal_g", "kmap",
-                                                          "logits", "normal_d")))
+    fu = flat_upstream(up)
+    loss = sum((o * fu[k]).sum() for o, k in zip(outs, ("rgb", "depth", "normal_g", "kmap",
+                                                        "logits", "normal_d")))
     loss.backward()
+    names = ("mean", "quat", "scale", "opacity", "kfac", "sh", "sem")
+    auto = {k: t.grad for k, t in zip(names, ds.tensors())}
+    check_grad_errors(grad_errors(auto, gref), tol=3e-3, norm=3e-4)
     r2 = rz.Renderer(rz.DeviceScene.from_scene(sc), cams)
     o2 = r2.forward()
-    g2 = r2.backward(o2, up)
-    # the two runs differ only in the order of the float32 atomic additions
-    for k, t in zip(("mean", "quat", "scale", "opacity", "kfac", "sh", "sem"), ds.tensors()):
-        a, b = t.grad.float(), g2[k]
+    g2 = r2.backward(o2, fu)
+    for k in names:
+        a, b = auto[k].float(), g2[k]
         rms = float(b.pow(2).mean().sqrt())
         rel = ((a - b).abs() / torch.clamp(b.abs(), min=1e-2 * rms + 1e-30)).max().item()
         assert rel < 1e-3, (k, rel)
@@ -284,7 +303,10 @@ def test_full_size_sampled_pixels(bf16):
     TX = (cam.width + 15) // 16
     views = {k: r.split(out[k], c)[0].cpu().numpy() for k, c in
              (("rgb", 3), ("depth", 1), ("normal_g", 3), ("kmap", 1), ("logits", 64))}
-    worst = {k: 0.0 for k in views}
+    okey = {"rgb": "rgb", "depth": "depth", "normal_g": "normal", "kmap": "kmap",
+            "logits": "logits"}
+    got = {k: [] for k in views}
+    exp = {k: [] for k in views}
     n_amb = 0
     for _ in range(300):
         u, v = int(rng.integers(0, cam.width)), int(rng.integers(0, cam.height))
@@ -297,18 +319,14 @@ def test_full_size_sampled_pixels(bf16):
         if bool(rr["amb_fwd"][0]):
             n_amb += 1
             continue
-        for k, key in (("rgb", "rgb"), ("normal_g", "normal"), ("kmap", "kmap")):
-            g = views[k][..., v, u]
-            worst[k] = max(worst[k], float(np.abs(g - rr[key][0].numpy()).max()))
-        d_ref = rr["depth"][0].item()
-        worst["depth"] = max(worst["depth"], abs(views["depth"][v, u] - d_ref) / max(abs(d_ref), 1.0))
-        lg = rr["logits"][0].numpy()
-        worst["logits"] = max(worst["logits"], float(np.abs(views["logits"][:, v, u] - lg).max()
-                                                      / max(np.sqrt(np.mean(lg ** 2)), 1e-3)))
+        for k in views:
+            got[k].append(np.atleast_1d(views[k][..., v, u]))
+            exp[k].append(np.atleast_1d(rr[okey[k]][0].numpy()))
+    worst = sampled_errors(got, exp)
     print("full-size sampled", worst, "ambiguous", n_amb)
-    assert n_amb < 30
+    assert n_amb <= 3
     assert worst["rgb"] < TOL_ABS and worst["normal_g"] < TOL_ABS and worst["kmap"] < TOL_ABS
-    assert worst["depth"] < TOL_REL and worst["logits"] < 10 * TOL_REL
+    assert worst["depth"] < TOL_REL and worst["logits"] < TOL_REL
 
 
 def test_full_size_finite_differences_64_params():
@@ -424,7 +442,7 @@ def test_full_size_finite_differences_64_params():
         an = float(g_gpu[name][idx])
         rel = abs(an - fd) / max(abs(fd), 1e-2 * rms[name])
         worst = max(worst, rel)
-        assert rel < 1e-2, (name, idx, an, fd, rms[name])
+        assert rel < 1e-3, (name, idx, an, fd, rms[name])
     print("FD 64 params: worst rel", worst)
 
 
@@ -481,3 +499,62 @@ def test_invalid_launch_shape_rejected():
     cfg.batch = 48
     with pytest.raises(abi.UnigsError):
         rz.Renderer(rz.DeviceScene.from_scene(sc), cams, cfg=cfg)
+
+
+def test_graph_replay_matches_per_call_path_and_oracle():
+    """The path the benchmark times (Alg. 2 and Alg. 4): preprocess, binning
+    without a host read-back (capacity mode), forward, normal from depth and
+    backward captured in one CUDA graph over 4 views of two resolutions with
+    BF16 features (tensor-core logit blend), then replayed twice.  Each
+    replay's forward outputs are bit-identical to the per-call path's, the
+    binning in the graph's workspace is bit-exact with the oracle, every
+    pixel of every view is within the forward tolerances of the oracle and
+    the gradients within the gradient criterion."""
+    sc, cams = scenes.small_room(n=6000, width=64, height=52, n_sem=16, seed=33, n_cams=4,
+                                 feat_bf16=True)
+    assert len({(c.width, c.height) for c in cams}) == 2
+    up, gref = _oracle_case(sc, cams, with_nd=False, seed=34)
+    _, ref_out, ref_b = oracle.render(sc, cams, with_normal_d=False)
+    fu = flat_upstream(up)
+    g_up = {k: fu[k] for k in fu if k != "normal_d"}
+    ds = rz.DeviceScene.from_scene(sc)
+    r0 = rz.Renderer(ds, cams)
+    out0 = r0.forward()
+    torch.cuda.synchronize()
+    r = rz.Renderer(ds, cams, capacity=r0.capacity)
+    out = r.alloc_outputs()
+    grads = r.alloc_grads()
+
+    def step():
+        r.forward(out, readback=False)
+        r.backward(out, g_up, grads=grads)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    for k in out:
+        out[k].fill_(-7.0) if out[k].is_floating_point() else out[k].fill_(7)
+    for v in grads.values():
+        v.fill_(-7.0)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for rep in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert r.status()[0] == 0
+        for k in ("rgb", "depth", "normal_g", "kmap", "logits", "T_final", "n_contrib",
+                  "normal_d"):
+            assert torch.equal(out[k], out0[k]), (rep, k)
+        keys, vals, ranges = r.sorted_instances()
+        assert np.array_equal(keys, ref_b["keys"]) and np.array_equal(vals, ref_b["vals"])
+        assert np.array_equal(ranges, ref_b["ranges"])
+        e = forward_errors(r, out, ref_out, sc.n_sem)
+        print("graph replay", rep, e)
+        assert e["ambiguous_fraction"] < MAX_AMBIGUOUS_FWD and e["n_contrib"] == 0
+        assert e["rgb"] < TOL_ABS and e["normal_g"] < TOL_ABS and e["kmap"] < TOL_ABS
+        assert e["T_final"] < TOL_ABS and e["depth"] < TOL_REL and e["logits"] < TOL_REL
+        check_grad_errors(grad_errors(grads, gref), norm=3e-4)

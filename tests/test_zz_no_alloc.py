@@ -1,4 +1,4 @@
-"""The allocation-free sort entry point against the workspace sort.
+"""The allocation-free sort entry point against the workspace sort and numpy.
 
 unigs_sort_pairs_static serves callers that cannot allocate device memory
 where they call (fixed memory budgets, plugin hosts that own allocation,
@@ -6,7 +6,8 @@ real-time loops): it takes only inputs and outputs and keeps its scratch in a
 static device array of the library.  Here its output must equal, bit for bit,
 the sorted (tile | depth, Gaussian) pairs that unigs_bin_sort produces in the
 caller's workspace, on two calls in a row (the second call finds the first
-call's data in the shared array).  This file is collected last.
+call's data in the shared array), and on random keys against numpy's stable
+argsort.  This file is collected last.
 """
 import numpy as np
 import pytest
@@ -64,6 +65,60 @@ def test_static_sort_matches_workspace_sort_twice():
         got_k, got_v = _static_sort(in_k, in_v, bits)
         assert np.array_equal(got_k, ref_k)
         assert np.array_equal(got_v, ref_v)
+
+
+@pytest.mark.parametrize("n,key_bits,garbage", [
+    (50_000, 41, True),                              # 6 passes (even), 1-bit last digit
+    (70_001, 33, True),                              # 5 passes, bits 33..63 ignored
+    (200_000, 48, True),                             # 6 whole-byte passes
+    (abi.UNIGS_STATIC_SORT_MAX_PAIRS, 64, False),    # 8 passes at the maximum size
+])
+def test_static_sort_against_numpy_stable_argsort(n, key_bits, garbage):
+    """Random keys, sorted by their low key_bits bits, against numpy's stable
+    argsort of (key mod 2^key_bits); with ``garbage`` every key also carries
+    random bits at and above key_bits, which must not decide the order (the
+    output keys are the input keys unchanged).  Many ties: the low bits are
+    drawn from a narrow range so that stability is exercised."""
+    rng = np.random.default_rng(n + key_bits)
+    mask = np.uint64((1 << key_bits) - 1) if key_bits < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    low = rng.integers(0, 1 << min(key_bits, 20), size=n, dtype=np.uint64)
+    if key_bits > 20:
+        low = low << np.uint64(key_bits - 20)      # ties in the bits below
+    keys = low & mask
+    if garbage:
+        hi = rng.integers(0, 1 << 62, size=n, dtype=np.uint64) << np.uint64(2)
+        keys = keys | (hi & ~mask)
+    if key_bits == 64:
+        keys = rng.integers(0, 1 << 63, size=n, dtype=np.uint64) * np.uint64(2) + \
+            rng.integers(0, 2, size=n, dtype=np.uint64)
+    vals = rng.permutation(n).astype(np.uint32)
+    order = np.argsort(keys & mask, kind="stable")
+    for _ in range(2):                 # the second call finds the first call's data
+        got_k, got_v = _static_sort(keys, vals, key_bits)
+        assert np.array_equal(got_k, keys[order])
+        assert np.array_equal(got_v, vals[order])
+
+
+def test_static_sort_rejects_overlapping_outputs():
+    """An output sharing any byte with an input or with the other output is
+    rejected before anything runs (not only exact aliases)."""
+    buf = torch.zeros(64, dtype=torch.int64, device="cuda")
+    vb = torch.zeros(64, dtype=torch.int32, device="cuda")
+    base, vbase = buf.data_ptr(), vb.data_ptr()
+    n = 16
+    cases = [
+        (base, vbase, base + 8 * 8, vbase + 4 * 32),   # keys_out overlaps keys_in
+        (base, vbase, base + 8 * 32, vbase + 4 * 8),   # vals_out overlaps vals_in
+        (base, vbase, base + 8 * 32, base + 8 * 40),   # vals_out inside keys_out
+        (base, base + 8 * 40, base + 8 * 36, vbase),   # keys_out overlaps vals_in
+    ]
+    for kin, vin, kout, vout in cases:
+        assert abi.unigs_sort_pairs_static(kin, vin, n, 40, kout, vout, None) == \
+            abi.UNIGS_ERR_INVALID_ARG
+    # disjoint buffers are accepted
+    assert abi.unigs_sort_pairs_static(base, vbase, n, 40, base + 8 * 32, vbase + 4 * 32,
+                                       None) == abi.UNIGS_OK
+    torch.cuda.synchronize()
 
 
 def test_static_sort_rejects_oversized_and_aliased_inputs():
