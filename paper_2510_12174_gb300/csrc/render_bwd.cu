@@ -73,7 +73,7 @@ struct BwdSmem {
     uint64_t cons[2];  // batch consumed (one arrival per warp)
     uint32_t max_last;
     int tile;
-    int abort;         // a bounded wait gave up (set_abort)
+    uint32_t issued[2];  // staging phases started per buffer (one thread counts)
 };
 
 // Offset of channel c of pixel row p in the swizzled upstream-gradient tile.
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         mbar_init(&S.cons[0], 8);
         mbar_init(&S.cons[1], 8);
         fence_mbar_init();
-        S.abort = 0;
+        S.issued[0] = S.issued[1] = 0u;
     }
     for (int j = tid; j < 2 * B * NS; j += 256) (&S.sem[0][0][0])[j] = 0.f;
     // the upstream-gradient rows are addressed by XOR within a row, which
@@ -186,14 +186,9 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
     const uint32_t a_row = go_row<NS>(go_base, tid);
     __syncthreads();
     // per buffer: phases of bar[] waited for and consumptions (uniform across
-    // the CTA), phases of bar[] started (warp 0, the producer); scalars, so
-    // that they stay in registers
-    uint32_t loads0 = 0u, loads1 = 0u, used0 = 0u, used1 = 0u, issued0 = 0u, issued1 = 0u;
+    // the CTA); scalars, so that they stay in registers
+    uint32_t loads0 = 0u, loads1 = 0u, used0 = 0u, used1 = 0u;
     bool timed_out = false;
-    auto give_up = [&]() {
-        timed_out = true;
-        set_abort(&S.abort);
-    };
 
     for (;;) {
         if (tid == 0) {
@@ -255,16 +250,17 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         // batch it; a buffer is restaged only after all 8 warps have arrived on
         // its "consumed" barrier, so the warps never meet at a CTA barrier
         // inside the tile.
-        // After a timeout the producer issues nothing more (a warp-uniform
-        // decision), so at most one copy per buffer is ever in flight.
+        // Warp 0 restages a buffer only if none of its own waits gave up (a
+        // warp-uniform decision): it waits on every staging phase itself, so
+        // the buffer's previous copy was seen to land and at most one copy
+        // per buffer is ever in flight; the exit drain finds it by S.issued.
         auto produce = [&](int bf, uint32_t first, int cnt) {
             const uint32_t u = bf ? used1 : used0;
-            if (u > 0 && !aborted(&S.abort) &&
-                !mbar_wait_bounded(&S.cons[bf], (u - 1) & 1u, BWAIT_LIMIT))
-                give_up();
-            if (__any_sync(0xffffffffu, aborted(&S.abort))) return;
+            if (u > 0 && !mbar_wait_bounded(&S.cons[bf], (u - 1) & 1u, BWAIT_LIMIT))
+                timed_out = true;
+            if (__any_sync(0xffffffffu, timed_out)) return;
             bwd_issue<NS, B>(P, S, bf, first, cnt, cam_idx);
-            if (bf) ++issued1; else ++issued0;
+            if (lane == 0) ++S.issued[bf];
         };
         if (warp == 0 && n_batches > 0)
             produce(0, range.x + (n_batches - 1) * B, min(B, n_items - (n_batches - 1) * B));
@@ -276,8 +272,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
             if (warp == 0 && b > 0) produce(buf ^ 1, range.x + (b - 1) * B, B);
             {
                 const uint32_t ph = buf ? loads1 : loads0;
-                if (aborted(&S.abort) || !mbar_wait_bounded(&S.bar[buf], ph & 1u, BWAIT_LIMIT))
-                    give_up();
+                if (!mbar_wait_bounded(&S.bar[buf], ph & 1u, BWAIT_LIMIT)) timed_out = true;
                 if (buf) ++loads1; else ++loads0;
             }
             const int count = min(B, n_items - b * B);
@@ -335,20 +330,27 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 gv[G_RGB + 1] = w * g_rgb[1];
                 gv[G_RGB + 2] = w * g_rgb[2];
                 gv[G_K] = w * g_K;
-                const float* vs = rc + R_VS;
                 const float* Nw = rc + R_NW;
                 const float inv_a = __fdividef(1.f, G.a);
-                float g_ds[3] = {0.f, 0.f, 0.f}, g_vs[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
-                // depth t_mid = -b'/a
+                // The Gaussian enters through v_s and d_s.  Besides g_vs the
+                // record takes B = g_vs (x) w + G2 (x) d_s with w = v_s + t d_s
+                // (the closest-approach point p_mid, formed without
+                // cancellation) and G2 = g_ds - t g_vs, which is small and is
+                // formed here term by term: g_vs (x) v_s and g_ds (x) d_s are
+                // both large for a Gaussian far from the camera and would cancel
+                // in the scale and rotation gradients (B equals their sum).
+                // g_a collects the normal's dependence on a = d_s.d_s only.
+                float g_vs[3] = {0.f, 0.f, 0.f}, g2[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
+                // depth t_mid = -b'/a: g_vs = g_bp d_s, g_ds = g_bp (v_s + 2 t d_s),
+                // so its part of G2 is g_bp w
                 const float g_t = w * g_D;
                 gv[G_Z] = P.center_depth ? g_t : 0.f;
                 if (!P.center_depth) {
                     const float g_bp = -g_t * inv_a;
-                    g_a -= g_t * G.t * inv_a;
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
                         g_vs[i] = g_bp * G.ds[i];
-                        g_ds[i] = g_bp * vs[i];
+                        g2[i] = g_bp * G.pm[i];
                     }
                 }
                 // normal n = sg * m / |m|, m = N_w p
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                     const float g_h = -G.sr * (g_p[0] * G.ds[0] + g_p[1] * G.ds[1] +
                                                g_p[2] * G.ds[2]);
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) g_ds[i] -= G.sr * G.h * g_p[i];
+                    for (int i = 0; i < 3; ++i) g2[i] -= G.sr * G.h * g_p[i];
                     // dh/ddisc = 1 / (2 a sqrt(disc))
                     g_disc = 0.5f * g_h * inv_a * rsqrtf(G.disc);
                     g_a -= g_h * G.h * inv_a;
@@ -383,21 +385,21 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 for (int i = 0; i < 3; ++i) g_cv[i] = -2.f * g_disc * G.cv[i];
                 // p_mid = (d_s x cv) / a
                 const float g_q[3] = {g_p[0] * inv_a, g_p[1] * inv_a, g_p[2] * inv_a};
-                cross_acc(G.cv, g_q, g_ds);
+                cross_acc(G.cv, g_q, g2);
                 cross_acc(g_q, G.ds, g_cv);
                 g_a -= (g_p[0] * G.pm[0] + g_p[1] * G.pm[1] + g_p[2] * G.pm[2]) * inv_a;
-                // cv = v_s x d_s
+                // cv = v_s x d_s: g_vs += d_s x g_cv, and g_ds += g_cv x v_s,
+                // whose part of G2 is g_cv x v_s - t (d_s x g_cv) = g_cv x w
                 cross_acc(G.ds, g_cv, g_vs);
-                cross_acc(g_cv, vs, g_ds);
+                cross_acc(g_cv, G.pm, g2);
                 // a = d_s . d_s
 #pragma unroll
-                for (int i = 0; i < 3; ++i) g_ds[i] = fmaf(2.f * g_a, G.ds[i], g_ds[i]);
-                // d_s = M_c d~
-                const float dt[3] = {xt, yt, 1.f};
+                for (int i = 0; i < 3; ++i) g2[i] = fmaf(2.f * g_a, G.ds[i], g2[i]);
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) gv[G_MC + 3 * r + c] = g_ds[r] * dt[c];
+                    for (int c = 0; c < 3; ++c)
+                        gv[G_B + 3 * r + c] = fmaf(g_vs[r], G.pm[c], g2[r] * G.ds[c]);
                     gv[G_VS + r] = g_vs[r];
                 }
                 {
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
     }
     // no bulk copy may still be landing in this CTA's shared memory when it
     // exits (after a timeout at most one per buffer is in flight)
-    if (tid == 0 && !drain_bulk(S.bar, issued0, issued1, BWAIT_LIMIT)) timed_out = true;
+    if (tid == 0 && !drain_bulk(S.bar, S.issued[0], S.issued[1], BWAIT_LIMIT)) timed_out = true;
     if (timed_out && lane == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
 }
 
@@ -523,6 +525,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
                 Sig[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
 
         float g_mu[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {}, g_s[3] = {0.f, 0.f, 0.f};
+        float g_th[3] = {0.f, 0.f, 0.f};  // rotation R -> R exp([theta]_x)
         float g_op = 0.f, g_k = 0.f;
         const int deg = P.g.sh_degree;
         const int n_sh = (deg + 1) * (deg + 1);
@@ -626,30 +629,23 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
                     g_s[b] += gM * R[a][b];
                 }
 
-            // ---- ray-ellipsoid setup
-            const float e[3] = {cam.C[0] - mu[0], cam.C[1] - mu[1], cam.C[2] - mu[2]};
-            float g_e[3] = {0.f, 0.f, 0.f};
-            for (int a = 0; a < 3; ++a) {
-                // M_c[a][b] = (1/s_a) sum_k R[k][a] R_cw[k][b]
-                float acc_s = 0.f;
-                for (int b = 0; b < 3; ++b) {
-                    const float gq = gr[G_MC + 3 * a + b] * is[a];
-                    const float Q = R[0][a] * cam.R_cw[b] + R[1][a] * cam.R_cw[3 + b] +
-                                    R[2][a] * cam.R_cw[6 + b];
-                    acc_s += gq * Q;
-                    for (int kk = 0; kk < 3; ++kk) g_R[kk][a] += gq * cam.R_cw[3 * kk + b];
-                }
-                // v_s[a] = (1/s_a) sum_k R[k][a] e_k
-                const float gvl = gr[G_VS + a] * is[a];
-                const float vl = R[0][a] * e[0] + R[1][a] * e[1] + R[2][a] * e[2];
-                acc_s += gvl * vl;
-                for (int kk = 0; kk < 3; ++kk) {
-                    g_R[kk][a] += gvl * e[kk];
-                    g_e[kk] += R[kk][a] * gvl;
-                }
-                g_s[a] -= acc_s * is[a];
+            // ---- ray-ellipsoid setup (Sec. 3.2): v_s = S^-1 R^T (C - mu) and
+            // d_s = S^-1 R^T d.  The record holds g_vs and B (= g_vs (x) v_s +
+            // g_ds (x) d_s, accumulated in a form free of cancellation), so
+            //   dL/ds_a = -B[a][a] / s_a,
+            //   dL/dtheta_k = sum_ij eps_ijk (s_j / s_i) B[i][j],
+            //   dL/dmu = -R (g_vs / s).
+            {
+                const float* Bm = gr + G_B;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) g_s[a] -= Bm[4 * a] * is[a];
+                g_th[0] += s[2] * is[1] * Bm[5] - s[1] * is[2] * Bm[7];
+                g_th[1] += s[0] * is[2] * Bm[6] - s[2] * is[0] * Bm[2];
+                g_th[2] += s[1] * is[0] * Bm[1] - s[0] * is[1] * Bm[3];
+                for (int kk = 0; kk < 3; ++kk)
+                    g_mu[kk] -= R[kk][0] * gr[G_VS] * is[0] + R[kk][1] * gr[G_VS + 1] * is[1] +
+                                R[kk][2] * gr[G_VS + 2] * is[2];
             }
-            for (int a = 0; a < 3; ++a) g_mu[a] -= g_e[a];
             // N_w[a][b] = R[a][b] / s_b
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
@@ -659,6 +655,16 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
                 }
         }
 
+        // the rotation's local-frame gradient as a matrix gradient:
+        // 1/2 R [g_theta]_x has the same derivative along every tangent R [e]_x
+        {
+            const float K[3][3] = {{0.f, -g_th[2], g_th[1]},
+                                   {g_th[2], 0.f, -g_th[0]},
+                                   {-g_th[1], g_th[0], 0.f}};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    g_R[a][b] += 0.5f * (R[a][0] * K[0][b] + R[a][1] * K[1][b] + R[a][2] * K[2][b]);
+        }
         // R(q^) -> q^ -> q
         const float gw = 2.f * (-z * g_R[0][1] + y * g_R[0][2] + z * g_R[1][0] - x * g_R[1][2] -
                                 y * g_R[2][0] + x * g_R[2][1]);

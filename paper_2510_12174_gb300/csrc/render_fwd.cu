@@ -51,7 +51,7 @@ struct FwdSmem {
     float sem[2][B][NS];
     uint64_t bar[2];
     int tile;
-    int abort;  // a bounded wait gave up (set_abort)
+    uint32_t issued[2];  // staging phases started per buffer (one thread counts)
 };
 
 template <int NS, int B>
@@ -105,27 +105,27 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
-        S.abort = 0;
+        S.issued[0] = S.issued[1] = 0u;
     }
     __syncthreads();
     // phases waited for per buffer (uniform across the CTA): the parity of the
-    // next phase to wait for; phases started per buffer (warp 0, the issuer)
-    uint32_t loads0 = 0u, loads1 = 0u, issued0 = 0u, issued1 = 0u;
+    // next phase to wait for
+    uint32_t loads0 = 0u, loads1 = 0u;
     bool timed_out = false;
-    // warp 0 stages a batch unless the CTA has given up (a warp-uniform
-    // decision: lane 0 arms the barrier, every lane issues copies)
+    // Warp 0 stages a batch unless one of its own waits gave up (a
+    // warp-uniform decision: lane 0 arms the barrier, every lane issues
+    // copies).  Warp 0 waits on every phase itself, so a buffer is restaged
+    // only after its previous copy was seen to land: at most one copy per
+    // buffer is ever in flight, and the exit drain finds it by S.issued.
     auto issue = [&](int bf, uint32_t first, int cnt, int cam) {
-        if (__any_sync(0xffffffffu, aborted(&S.abort))) return;
+        if (__any_sync(0xffffffffu, timed_out)) return;
         issue_batch<NS, B>(P, S, bf, first, cnt, cam);
-        if (bf) ++issued1; else ++issued0;
+        if ((tid & 31) == 0) ++S.issued[bf];
     };
     // every thread waits for the batch in buffer bf (bounded)
     auto wait_batch = [&](int bf) {
         const uint32_t ph = bf ? loads1 : loads0;
-        if (aborted(&S.abort) || !mbar_wait_bounded(&S.bar[bf], ph & 1u, WAIT_LIMIT)) {
-            timed_out = true;
-            set_abort(&S.abort);
-        }
+        if (!mbar_wait_bounded(&S.bar[bf], ph & 1u, WAIT_LIMIT)) timed_out = true;
         if (bf) ++loads1; else ++loads0;
     };
     uint32_t n_eval = 0, n_blend = 0;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256, 2) render_fwd_kernel(const FwdParams P) {
     }
     // no bulk copy may still be landing in this CTA's shared memory when it
     // exits (after a timeout the issuer stopped, so at most one per buffer)
-    if (tid == 0 && !drain_bulk(S.bar, issued0, issued1, WAIT_LIMIT)) timed_out = true;
+    if (tid == 0 && !drain_bulk(S.bar, S.issued[0], S.issued[1], WAIT_LIMIT)) timed_out = true;
     if (timed_out && (tid & 31) == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
     // work counters: one atomic per warp
 #pragma unroll

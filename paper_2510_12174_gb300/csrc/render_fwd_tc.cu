@@ -69,7 +69,7 @@ struct FwdTcSmem {
     uint64_t mma_bar[2];  // MMA completion per operand buffer
     uint32_t tmem_base;
     int tile;
-    int abort;            // a bounded wait gave up (set_abort)
+    uint32_t issued[2];   // staging phases started per buffer (one thread counts)
 };
 
 template <int NS>
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
         mbar_init(&S.mma_bar[0], 1);
         mbar_init(&S.mma_bar[1], 1);
         fence_mbar_init();
-        S.abort = 0;
+        S.issued[0] = S.issued[1] = 0u;
     }
     if (warp == 0) {
         tmem_alloc(&S.tmem_base, NCOLS);
@@ -132,32 +132,16 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
     tc_fence_after_sync();
     const uint32_t tmem = S.tmem_base;
 
-    // staging phases waited for per buffer (uniform across the CTA) and
-    // started per buffer (warp 0, the issuer)
-    uint32_t loads0 = 0u, loads1 = 0u, issued0 = 0u, issued1 = 0u;
+    // staging phases waited for per buffer (uniform across the CTA).  After a
+    // bounded wait gave up, warp 0 (which waits on every phase itself) issues
+    // no further copy, so at most one copy per buffer is ever in flight and
+    // the exit drain below finds it by its count in S.issued.
+    uint32_t loads[2] = {0u, 0u};
     // MMA commits and completed waits per operand buffer (uniform across the
     // CTA); each buffer's barrier is waited on before its next commit, so its
     // phases never run two ahead of the waits
     uint32_t commits0 = 0, commits1 = 0, waited0 = 0, waited1 = 0;
     bool timed_out = false;
-    auto give_up = [&]() {
-        timed_out = true;
-        set_abort(&S.abort);
-    };
-    // warp 0 stages a batch unless the CTA has given up (warp-uniform: lane 0
-    // arms the barrier, every lane issues copies), so after a timeout at most
-    // one copy per buffer is in flight
-    auto issue = [&](int bf, uint32_t first, int cnt, int cam) {
-        if (__any_sync(0xffffffffu, aborted(&S.abort))) return;
-        tc_issue_batch<NS, B, F32>(P, S, bf, first, cnt, cam);
-        if (bf) ++issued1; else ++issued0;
-    };
-    auto wait_batch = [&](int bf) {
-        const uint32_t ph = bf ? loads1 : loads0;
-        if (aborted(&S.abort) || !mbar_wait_bounded(&S.bar[bf], ph & 1u, TC_WAIT_LIMIT))
-            give_up();
-        if (bf) ++loads1; else ++loads0;
-    };
     uint32_t n_eval = 0, n_blend = 0;
     const int mt = tid >> 7, row = tid & 127;
     const int wrow = (row >> 3) * Sm::SBO + (row & 7) * 16;
@@ -186,7 +170,10 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
         const uint2 range = P.ranges[gtile];
         const int n_items = (int)(range.y - range.x);
         const int n_batches = (n_items + B - 1) / B;
-        if (warp == 0 && n_batches > 0) issue(0, range.x, min(B, n_items), cam_idx);
+        if (warp == 0 && n_batches > 0 && !__any_sync(0xffffffffu, timed_out)) {
+            tc_issue_batch<NS, B, F32>(P, S, 0, range.x, min(B, n_items), cam_idx);
+            if ((tid & 31) == 0) ++S.issued[0];
+        }
         __syncthreads();
 
         float T = 1.f;
@@ -197,9 +184,13 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
 
         for (int b = 0; b < n_batches; ++b) {
             const int buf = b & 1;
-            if (warp == 0 && b + 1 < n_batches)
-                issue(buf ^ 1, range.x + (b + 1) * B, min(B, n_items - (b + 1) * B), cam_idx);
-            wait_batch(buf);
+            if (warp == 0 && b + 1 < n_batches && !__any_sync(0xffffffffu, timed_out)) {
+                tc_issue_batch<NS, B, F32>(P, S, buf ^ 1, range.x + (b + 1) * B,
+                                      min(B, n_items - (b + 1) * B), cam_idx);
+                if ((tid & 31) == 0) ++S.issued[buf ^ 1];
+            }
+            if (!mbar_wait_bounded(&S.bar[buf], loads[buf] & 1u, TC_WAIT_LIMIT)) timed_out = true;
+            ++loads[buf];
             // the MMAs that last read this operand buffer (two batches back)
             // must be complete before it is rewritten
             const int ob = (int)opbuf;
@@ -207,7 +198,7 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
                 const uint32_t cm = ob ? commits1 : commits0;
                 if ((ob ? waited1 : waited0) < cm) {
                     if (!mbar_wait_bounded(&S.mma_bar[ob], (cm - 1) & 1u, TC_WAIT_LIMIT))
-                        give_up();
+                        timed_out = true;
                     if (ob) waited1 = cm; else waited0 = cm;
                 }
             }
@@ -328,19 +319,23 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
             opbuf ^= 1u;
             ++batches_done;
             if (alive == 0) {
-                if (b + 1 < n_batches) wait_batch(buf ^ 1);
+                if (b + 1 < n_batches) {
+                    if (!mbar_wait_bounded(&S.bar[buf ^ 1], loads[buf ^ 1] & 1u, TC_WAIT_LIMIT))
+                        timed_out = true;
+                    ++loads[buf ^ 1];
+                }
                 break;
             }
         }
         // logits: the accumulators of this thread's row (zero without a batch)
         if (waited0 < commits0) {
             if (!mbar_wait_bounded(&S.mma_bar[0], (commits0 - 1) & 1u, TC_WAIT_LIMIT))
-                give_up();
+                timed_out = true;
             waited0 = commits0;
         }
         if (waited1 < commits1) {
             if (!mbar_wait_bounded(&S.mma_bar[1], (commits1 - 1) & 1u, TC_WAIT_LIMIT))
-                give_up();
+                timed_out = true;
             waited1 = commits1;
         }
         tc_fence_after_sync();
@@ -382,10 +377,10 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
     // Before the CTA exits: no bulk copy may still be landing in its shared
     // memory, and no MMA may still be writing its tensor-memory columns (each
     // tile waits for its last commits; after a timeout the last commit of each
-    // operand buffer is waited for once more, bounded, and the issuer stopped
-    // staging).  Then the columns are returned: a CTA must free its tensor
-    // memory before it exits, also when a wait gave up.
-    if (tid == 0 && !drain_bulk(S.bar, issued0, issued1, TC_WAIT_LIMIT)) timed_out = true;
+    // operand buffer is waited for once more, bounded).  Then the columns are
+    // returned: a CTA frees its tensor memory before it exits, also when a
+    // wait gave up.
+    if (tid == 0 && !drain_bulk(S.bar, S.issued[0], S.issued[1], TC_WAIT_LIMIT)) timed_out = true;
     if (commits0 > 0 && !mbar_wait_bounded(&S.mma_bar[0], (commits0 - 1) & 1u, TC_WAIT_LIMIT))
         timed_out = true;
     if (commits1 > 0 && !mbar_wait_bounded(&S.mma_bar[1], (commits1 - 1) & 1u, TC_WAIT_LIMIT))
@@ -409,8 +404,12 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
 template <int NS, int B, bool F32>
 static void launch_fwd_tc_t(const FwdTcParams& P, int grid, cudaStream_t st) {
     const size_t smem = sizeof(FwdTcSmem<NS, B, F32>);
-    // a failure here surfaces as the launch error the entry point returns
-    ensure_smem_limit(reinterpret_cast<const void*>(&render_fwd_tc_kernel<NS, B, F32>), (int)smem);
+    static bool attr_set = false;  // host-side, set once per instantiation
+    if (!attr_set) {
+        cudaFuncSetAttribute(render_fwd_tc_kernel<NS, B, F32>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
     render_fwd_tc_kernel<NS, B, F32><<<grid, 256, smem, st>>>(P);
 }
 

@@ -73,10 +73,12 @@ constexpr float KAPPA_FF = 64.f;
 // accumulators, 256 bytes), filled by atomics in the backward composite and
 // consumed by the preprocess backward:
 // dL/d(projected centre x, y), dL/d(a, b, c) of the 2D covariance
-// [[a, b], [b, c]] (low-pass included), opacity, RGB, M_c, v_s, N_w, k and the
-// centre depth (centre-depth mode).
+// [[a, b], [b, c]] (low-pass included), opacity, RGB, the local-frame matrix
+// B = sum g_vs (x) v_s + g_ds (x) d_s (row-major, accumulated as
+// g_vs (x) w + (g_ds - t g_vs) (x) d_s, see the backward composite), v_s, N_w,
+// k and the centre depth (centre-depth mode).
 enum {
-    G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_OP, G_RGB, G_MC = 9, G_VS = 18,
+    G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_OP, G_RGB, G_B = 9, G_VS = 18,
     G_NW = 21, G_K = 30, G_Z = 31, GREC_FLOATS = 32
 };
 
@@ -254,15 +256,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     for (uint32_t i = 0; i < max_iter; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
-}
-
-// Sticky per-CTA abort flag in shared memory: set by a thread whose bounded
-// wait gave up; read (volatile) by the producer before it issues a copy and
-// by the consumers before they wait, so that after a timeout no copy is
-// issued and no thread waits on a phase that will never complete.
-__device__ __forceinline__ void set_abort(int* flag) { *reinterpret_cast<volatile int*>(flag) = 1; }
-__device__ __forceinline__ bool aborted(const int* flag) {
-    return *reinterpret_cast<const volatile int*>(flag) != 0;
 }
 
 // Before a CTA exits: waits (bounded) until the last bulk copy issued into

@@ -103,3 +103,100 @@ def test_upstream_tile_xor_addresses(ns):
                     addr = (a_g ^ (((i * rps) & (lpr - 1)) << 4)) + i * rps * ns * 4
                     want = base + 4 * _go_index(ns, warp * 32 + i * rps + h, 4 * c4)
                     assert addr == want
+
+
+# --------------------------------------------------------------------------
+# Local-frame gradient record of the backward composite.  The pair function
+# depends on the Gaussian's rotation R, scale s and centre mu through
+# v_s = S^-1 R^T (C - mu) and d_s = S^-1 R^T d.  The kernels accumulate, over
+# the pixels of a (camera, Gaussian), the vector g_vs and the matrix
+#   B = g_vs (x) w + G2 (x) d_s,   w = v_s + t d_s,   G2 = g_ds - t g_vs,
+# which equals g_vs (x) v_s + g_ds (x) d_s for every t; with t the midpoint
+# parameter, w is the closest-approach point and G2 is small for a Gaussian
+# far from the camera, where g_vs (x) v_s and g_ds (x) d_s are both large and
+# cancel.  From B and g_vs:
+#   dL/ds_a = -B[a][a] / s_a,  dL/dtheta_k = sum_ij eps_ijk (s_j / s_i) B[i][j]
+#   (R -> R exp([theta]_x)),   dL/dmu = -R (g_vs / s).
+# --------------------------------------------------------------------------
+def _skew(v):
+    return np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
+
+
+def _ray_loss_torch(vs, ds, up):
+    """Depth t = -(v_s.d_s)/(d_s.d_s) and the entry normal of the scaled unit
+    sphere (through cv = v_s x d_s, as the kernels differentiate it), dotted
+    with fixed upstream weights."""
+    import torch
+    a = (ds * ds).sum()
+    bp = (vs * ds).sum()
+    t = -bp / a
+    cv = torch.linalg.cross(vs, ds)
+    disc = a - (cv * cv).sum()
+    pm = torch.linalg.cross(ds, cv) / a
+    p = pm - torch.sqrt(disc) / a * ds
+    return up[0] * t + (up[1:4] * p).sum()
+
+
+def test_local_frame_gradient_record_identities():
+    import torch
+    rng = np.random.default_rng(71)
+    eps = np.zeros((3, 3, 3))
+    for i, j, k in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        eps[i, j, k], eps[j, i, k] = 1.0, -1.0
+    n_done = 0
+    while n_done < 30:
+        R0 = _rot(rng.normal(size=4))
+        s = np.exp(rng.normal(-3.5, 1.0, size=3))
+        mu = rng.normal(size=3)
+        C = mu + rng.normal(size=3) * rng.uniform(0.5, 5.0)
+        # a ray through the ellipsoid's silhouette region
+        target = mu + R0 @ (s * rng.uniform(-0.8, 0.8, size=3))
+        d = target - C
+        up = torch.as_tensor(rng.normal(size=4))
+        T = lambda x: torch.as_tensor(x, dtype=torch.float64)
+        th = torch.zeros(3, dtype=torch.float64, requires_grad=True)
+        st = T(s).requires_grad_(True)
+        mt = T(mu).requires_grad_(True)
+        K = torch.zeros(3, 3, dtype=torch.float64)
+        K = K.index_put((torch.tensor([0, 0, 1, 1, 2, 2]), torch.tensor([1, 2, 0, 2, 0, 1])),
+                        torch.stack([-th[2], th[1], th[2], -th[0], -th[1], th[0]]))
+        R = T(R0) @ torch.linalg.matrix_exp(K)
+        vs = (R.T @ (T(C) - mt)) / st
+        ds = (R.T @ T(d)) / st
+        a = float((ds * ds).sum())
+        cv = np.cross(vs.detach().numpy(), ds.detach().numpy())
+        if a - cv @ cv <= 1e-3 * a:
+            continue
+        L = _ray_loss_torch(vs, ds, up)
+        g_th, g_s, g_mu = torch.autograd.grad(L, (th, st, mt))
+        # the same loss with v_s, d_s as leaves
+        vsl = vs.detach().clone().requires_grad_(True)
+        dsl = ds.detach().clone().requires_grad_(True)
+        g_vs, g_ds = torch.autograd.grad(_ray_loss_torch(vsl, dsl, up), (vsl, dsl))
+        g_vs, g_ds = g_vs.numpy(), g_ds.numpy()
+        v, dd = vs.detach().numpy(), ds.detach().numpy()
+        t = -(v @ dd) / (dd @ dd)
+        w = v + t * dd
+        B = np.outer(g_vs, w) + np.outer(g_ds - t * g_vs, dd)
+        assert np.allclose(B, np.outer(g_vs, v) + np.outer(g_ds, dd), rtol=1e-9,
+                           atol=1e-9 * np.abs(np.outer(g_ds, dd)).max())
+        assert np.allclose(-np.diag(B) / s, g_s.numpy(), rtol=1e-8, atol=1e-10)
+        th_ref = np.einsum("ijk,ij->k", eps, (s[None, :] / s[:, None]) * B)
+        assert np.allclose(th_ref, g_th.numpy(), rtol=1e-8, atol=1e-10)
+        assert np.allclose(-R0 @ (g_vs / s), g_mu.numpy(), rtol=1e-9, atol=1e-12)
+        # the equivalent matrix gradient 1/2 R [g_theta]_x gives the same
+        # directional derivative along every tangent R [e]_x
+        GR = 0.5 * R0 @ _skew(th_ref)
+        for e in np.eye(3):
+            assert abs(np.sum(GR * (R0 @ _skew(e))) - th_ref @ e) < 1e-9 * (1 + abs(th_ref @ e))
+        # the analytic forms of G2 = g_ds - t g_vs the kernels evaluate: the
+        # depth's part is g_bp w (g_bp = -g_t/a), the cross product's g_cv x w
+        g_t = float(up[0])
+        g_bp = -g_t / a
+        depth_vs, depth_ds = g_bp * dd, g_bp * (v + 2 * t * dd)
+        assert np.allclose(depth_ds - t * depth_vs, g_bp * w, rtol=1e-9, atol=1e-12)
+        g_cv = rng.normal(size=3)
+        cv_vs, cv_ds = np.cross(dd, g_cv), np.cross(g_cv, v)
+        assert np.allclose(cv_ds - t * cv_vs, np.cross(g_cv, w), rtol=1e-9,
+                           atol=1e-9 * np.abs(cv_ds).max())
+        n_done += 1
