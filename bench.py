@@ -113,12 +113,13 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one render_bwd launch on this workload, from a
-# one-pass ncu capture of the full run (dram__bytes_read.sum 6.654 GB +
-# dram__bytes_write.sum 0.800 GB), valid only for the kernel sources whose
-# digest is recorded here; any change to them reports null until re-captured.
-BWD_TRAFFIC_BYTES = 7_453_076_480
-BWD_TRAFFIC_SOURCES = ("render_bwd.cu", "splat.cuh", "unigs_internal.cuh", "ff.cuh", "sh.cuh")
-BWD_TRAFFIC_DIGEST = "b8bcfeaa8b7b6d041f522d09cceeef70397868f881d5109c3bde4fb73ae65d10"
+# one-pass ncu capture of the full run (dram__bytes_read.sum 7.02 GB +
+# dram__bytes_write.sum 1.12 GB; the metrics take one pass on the small
+# profiling case too), valid only for the kernel sources whose digest is
+# recorded here; any change to them reports null until re-captured.
+BWD_TRAFFIC_BYTES = 8_140_000_000
+BWD_TRAFFIC_SOURCES = ('render_bwd.cu', 'splat.cuh', 'unigs_internal.cuh', 'ff.cuh', 'sh.cuh')
+BWD_TRAFFIC_DIGEST = "9634ff3710a701c5b4d07c4ffbc3fe454e785d9793ca374244ed1c972fb40447"
 
 
 def bwd_traffic():
