@@ -34,8 +34,10 @@
  *   camera frame is ((u - cx)/fx, (v - cy)/fy, 1) (Eq. computeRay; the
  *   supplement's back-projection uses cx = W/2, cy = H/2).  Camera frame: x
  *   right, y down, z forward.
- * - Tiles are 16 x 16 pixels, numbered per camera row-major and offset by
- *   the tiles of the preceding cameras (global tile id).
+ * - Tiles are tile_w x tile_h pixels (unigs_config; 16 x 16 by default, or
+ *   8 x 32, 32 x 8, 64 x 4: always 256 pixels, one per thread of a composite
+ *   CTA), numbered per camera row-major and offset by the tiles of the
+ *   preceding cameras (global tile id).
  */
 #ifndef UNIGS_H
 #define UNIGS_H
@@ -50,7 +52,8 @@ extern "C" {
 typedef struct CUstream_st* unigs_stream; /* a cudaStream_t; NULL = legacy default */
 
 #define UNIGS_MAX_CAMS 64
-#define UNIGS_TILE 16
+#define UNIGS_TILE 16         /* default tile side */
+#define UNIGS_TILE_PIXELS 256 /* pixels of every tile shape */
 #define UNIGS_MAX_SEM 64
 
 typedef enum {
@@ -165,6 +168,16 @@ typedef struct {
     int32_t ctas_per_sm_fwd; /* forward composite, 1..8 (the tensor-core path
                              caps it at 4); 0 = 4 on the tensor-core path, 2
                              on the FP32 pipes */
+    int32_t tile_w, tile_h; /* tile shape in pixels: 16 x 16 (0 x 0 = 16 x 16),
+                             8 x 32, 32 x 8 or 64 x 4.  It sets which (tile,
+                             Gaussian) pairs are listed and the schedule, not
+                             the rendered result: a Gaussian is drawn on the
+                             pixels of its 3-sigma square (not on whole tiles),
+                             so every pixel blends the same Gaussians in the
+                             same order for every shape.  n_contrib (a position
+                             in the tile's list) and the float32 summation
+                             order of the tensor-core logit blend and of the
+                             backward's atomics do depend on it */
 } unigs_config;
 
 #define UNIGS_FLAG_CENTER_DEPTH 1u
@@ -193,9 +206,11 @@ void unigs_config_default(unigs_config* cfg);
 
 /* Validates the sizes, fills *plan and its workspace size.  instance_capacity
  * bounds the number of (tile, Gaussian) pairs over all cameras (the 3DGS
- * duplication step); 0 picks 4 * n * n_cams.  cams is host memory.
+ * duplication step); 0 picks 4 * n * n_cams.  cams is host memory.  The
+ * plan's cfg holds the resolved tile shape (16 x 16 for 0 x 0).
  * Returns UNIGS_ERR_INVALID_ARG on n < 0, n_cams outside 1..UNIGS_MAX_CAMS,
- * an empty image, sh_degree outside 0..3, n_sem outside 0..64. */
+ * an empty image, sh_degree outside 0..3, n_sem outside 0..64, a tile shape
+ * other than the four listed in unigs_config. */
 unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g,
                              const unigs_camera* cams, int32_t n_cams,
                              const unigs_config* cfg, int64_t instance_capacity);
@@ -227,7 +242,9 @@ unigs_status unigs_bin_sort(const unigs_plan* plan, void* ws, int64_t* n_instanc
                             unigs_stream stream);
 
 /* Forward composite, Alg. 2 (T initialised to 1; k blended, not t; colour
- * from SH): persistent CTAs pull 16x16 tiles longest list first, Gaussian
+ * from SH; each Gaussian truncated to its 3-sigma square |u - m_x| <= r,
+ * |v - m_y| <= r with r = ceil(3 sqrt(lambda_max)) of the binning recipe, the
+ * 3DGS radius applied per pixel): persistent CTAs pull tiles longest list first, Gaussian
  * batches staged in shared memory by bulk (TMA) copies, per-pixel
  * accumulators in registers, early exit when every pixel of the tile has
  * T < T_min.  With 9..64 logits (and without UNIGS_FLAG_SIMT_LOGITS) the

@@ -32,10 +32,11 @@ PARAM_KEYS = ("mean", "quat", "scale", "opacity", "kfac", "sh", "sem")
 def render(scene, cams, requires_grad: bool = False, binning=None,
            tiles: Optional[Sequence[Sequence[int]]] = None,
            bands: Optional[Bands] = None, with_normal_d: bool = True,
-           center_depth: bool = False):
-    """Forward over all cameras.  Returns (params, per-camera outputs, binning)."""
+           center_depth: bool = False, tile=(16, 16)):
+    """Forward over all cameras.  Returns (params, per-camera outputs, binning).
+    ``tile`` = (TW, TH) is the tile shape of the binning when none is given."""
     if binning is None:
-        binning = bin_cameras_fast(scene, cams)
+        binning = bin_cameras_fast(scene, cams, tile)
     params = Params.from_scene(scene, requires_grad)
     outs = []
     ctx = torch.enable_grad() if requires_grad else torch.no_grad()
@@ -56,7 +57,7 @@ def render(scene, cams, requires_grad: bool = False, binning=None,
 
 def render_and_grad(scene, cams, upstream: Dict[str, List[np.ndarray]],
                     binning=None, bands: Optional[Bands] = None, center_depth: bool = False,
-                    tiles: Optional[Sequence[Sequence[int]]] = None):
+                    tiles: Optional[Sequence[Sequence[int]]] = None, tile=(16, 16)):
     """Forward plus exact gradients of L = sum_c <output_c, upstream_c>.
 
     ``upstream`` maps rgb, depth, normal_g, kmap, logits, normal_d to per-camera
@@ -64,7 +65,8 @@ def render_and_grad(scene, cams, upstream: Dict[str, List[np.ndarray]],
     grads keyed like the Gaussian parameters.
     """
     params, outs, binning = render(scene, cams, requires_grad=True, binning=binning,
-                                   bands=bands, center_depth=center_depth, tiles=tiles)
+                                   bands=bands, center_depth=center_depth, tiles=tiles,
+                                   tile=tile)
     loss = torch.zeros((), dtype=torch.float64)
     name = {"rgb": "rgb", "depth": "depth", "normal_g": "normal", "kmap": "kmap",
             "logits": "logits", "normal_d": "normal_d"}

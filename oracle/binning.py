@@ -34,8 +34,8 @@ The recipe, per (camera, Gaussian); (+) and (*) are float32 add and multiply:
   mid = 0.5*(a + c) ; lam = mid + sqrt(max(0.1, mid*mid - det))
   r   = ceil(3 * sqrt(lam))                          (3-sigma radius, pixels)
   m_x = fx*(px*iz) + cx ; m_y = fy*(py*iz) + cy     (projected centre)
-  rect: x0 = clamp(floor((m_x - r) / 16), 0, TX), x1 = clamp(ceil((m_x + r) / 16), 0, TX)
-        (same for y with TY); cull if the rectangle is empty
+  rect: x0 = clamp(floor((m_x - r) / TW), 0, TX), x1 = clamp(ceil((m_x + r) / TW), 0, TX)
+        (same for y with TH and TY); cull if the rectangle is empty
   key  = (global tile id << 32) | float32 bits of p_c.z
 
 Opacity-aware tile test.  Alg. 2 skips a Gaussian at a pixel where its alpha
@@ -48,7 +48,7 @@ ln(255 op) <= e*LN2 + (m - 1) (ln m <= m - 1), so
   qlim = (2 (e*LN2 + (m - 1))) * 1.01 + 0.05      (LN2 = float32(ln 2), margin
                                                   for float32 evaluation)
 and a rectangle tile is kept iff the minimum of q over the tile's pixel-centre
-square [16tx, 16tx+15] x [16ty, 16ty+15] is <= qlim.  That minimum is 0 when
+rectangle [TW tx, TW tx + TW-1] x [TH ty, TH ty + TH-1] is <= qlim.  That minimum is 0 when
 the centre lies in the square, else the least of the four edge minima: on a
 vertical edge x = xe, dx = xe - m_x, dy = clamp(-(kB*dx)/kC, Y0 - m_y, Y1 - m_y)
 (and symmetrically on horizontal edges), q = ((kA*dx)*dx + ((2*kB)*dx)*dy)
@@ -60,6 +60,10 @@ result is the one the full rectangle gives.
 Within a tile the list is ordered by (depth bits, Gaussian index): a stable
 sort by the 64-bit key of the instances emitted in (camera, Gaussian, tile
 row-major) order.
+
+Tiles are TW x TH pixels (16 x 16 by default; the library also takes 8 x 32,
+32 x 8 and 64 x 4), TX = ceil(W / TW) and TY = ceil(H / TH) per camera.  The
+divisions by TW and TH are by powers of two, hence exact.
 """
 from __future__ import annotations
 
@@ -67,11 +71,12 @@ import numpy as np
 
 f32 = np.float32
 TILE = 16
+DEFAULT_TILE = (TILE, TILE)
 
 
-def _rect_axis(m, r, n_tiles):
-    lo = np.floor((m - r) / f32(TILE))
-    hi = np.ceil((m + r) / f32(TILE))
+def _rect_axis(m, r, n_tiles, side):
+    lo = np.floor((m - r) / f32(side))
+    hi = np.ceil((m + r) / f32(side))
     nt = f32(n_tiles)
     lo = np.fmin(np.fmax(lo, f32(0)), nt)
     hi = np.fmin(np.fmax(hi, f32(0)), nt)
@@ -87,10 +92,11 @@ def tile_keep(pr, g, tx, ty):
     mx, my = pr["mean2d"][0][g], pr["mean2d"][1][g]
     kA, kB, kC = pr["conic32"][0][g], pr["conic32"][1][g], pr["conic32"][2][g]
     qlim = pr["qlim"][g]
-    X0 = (tx * TILE).astype(f32)
-    X1 = (tx * TILE + (TILE - 1)).astype(f32)
-    Y0 = (ty * TILE).astype(f32)
-    Y1 = (ty * TILE + (TILE - 1)).astype(f32)
+    tw, th = pr["tile"]
+    X0 = (tx * tw).astype(f32)
+    X1 = (tx * tw + (tw - 1)).astype(f32)
+    Y0 = (ty * th).astype(f32)
+    Y1 = (ty * th + (th - 1)).astype(f32)
     two = f32(2)
     with np.errstate(all="ignore"):
         def qf(dx, dy):
@@ -112,9 +118,10 @@ def tile_keep(pr, g, tx, ty):
     return pr["no_cull"][g] | (qmin <= qlim)
 
 
-def project_fp32(scene, cam, tile: int = TILE) -> dict:
-    """Float32 recipe for one camera.  Returns per-Gaussian arrays."""
-    assert tile == TILE
+def project_fp32(scene, cam, tile=DEFAULT_TILE) -> dict:
+    """Float32 recipe for one camera with tiles of tile = (TW, TH) pixels.
+    Returns per-Gaussian arrays."""
+    tile_w, tile_h = int(tile[0]), int(tile[1])
     with np.errstate(all="ignore"):
         mu = scene.mean.astype(f32)
         Rw = cam.R_wc.astype(f32)
@@ -166,10 +173,10 @@ def project_fp32(scene, cam, tile: int = TILE) -> dict:
         r = np.ceil(f32(3) * np.sqrt(lam))
         mx = fx * xz + cx
         my = fy * yz + cy
-        TX = (cam.width + TILE - 1) // TILE
-        TY = (cam.height + TILE - 1) // TILE
-        x0, x1 = _rect_axis(mx, r, TX)
-        y0, y1 = _rect_axis(my, r, TY)
+        TX = (cam.width + tile_w - 1) // tile_w
+        TY = (cam.height + tile_h - 1) // tile_h
+        x0, x1 = _rect_axis(mx, r, TX, tile_w)
+        y0, y1 = _rect_axis(my, r, TY, tile_h)
         valid = in_front & qok & det_ok & (x1 > x0) & (y1 > y0)
         # opacity-aware tile test (module docstring)
         kA = c / det
@@ -187,7 +194,7 @@ def project_fp32(scene, cam, tile: int = TILE) -> dict:
     pr = dict(p_c=np.stack(p), z=pz, zbits=zbits, cov2d=np.stack([a, b, c]),
               det=det, radius=r, mean2d=np.stack([mx, my]),
               rect=np.stack([x0, x1, y0, y1]), valid=valid, tiles_x=TX, tiles_y=TY,
-              conic32=np.stack([kA, kB, kC]), qlim=qlim, no_cull=no_cull)
+              conic32=np.stack([kA, kB, kC]), qlim=qlim, no_cull=no_cull, tile=(tile_w, tile_h))
     # tiles kept per Gaussian
     touched = np.zeros(pz.shape[0], dtype=np.int64)
     idx = np.nonzero(valid)[0]
@@ -213,14 +220,15 @@ def _rect_tiles(pr, idx):
     return idx[rep], tx, ty
 
 
-def bin_cameras(scene, cams) -> dict:
+def bin_cameras(scene, cams, tile=DEFAULT_TILE) -> dict:
     """Binning over several cameras with global tile ids.
 
     Camera k's tiles are numbered tile_offset[k] + ty * TX_k + tx.  Returns the
     sorted 64-bit keys, the Gaussian index of each instance (``vals``), the
-    per-tile [start, end) ranges and the per-camera projections.
+    per-tile [start, end) ranges, the per-camera projections and the tile
+    shape.
     """
-    projs = [project_fp32(scene, c) for c in cams]
+    projs = [project_fp32(scene, c, tile) for c in cams]
     tile_off = [0]
     for pr in projs:
         tile_off.append(tile_off[-1] + pr["tiles_x"] * pr["tiles_y"])
@@ -251,12 +259,12 @@ def bin_cameras(scene, cams) -> dict:
     ends = np.searchsorted(tiles, np.arange(n_tiles), side="right")
     ranges = np.stack([starts, ends], axis=1).astype(np.uint32)
     return dict(keys=keys, vals=vals, ranges=ranges, tile_offset=np.array(tile_off),
-                projs=projs)
+                projs=projs, tile=tuple(int(t) for t in tile))
 
 
-def bin_cameras_fast(scene, cams) -> dict:
+def bin_cameras_fast(scene, cams, tile=DEFAULT_TILE) -> dict:
     """Same result as :func:`bin_cameras`, vectorised for large scenes."""
-    projs = [project_fp32(scene, c) for c in cams]
+    projs = [project_fp32(scene, c, tile) for c in cams]
     tile_off = [0]
     for pr in projs:
         tile_off.append(tile_off[-1] + pr["tiles_x"] * pr["tiles_y"])
@@ -281,4 +289,4 @@ def bin_cameras_fast(scene, cams) -> dict:
     ends = np.searchsorted(tiles, np.arange(n_tiles), side="right")
     ranges = np.stack([starts, ends], axis=1).astype(np.uint32)
     return dict(keys=keys, vals=vals, ranges=ranges, tile_offset=np.array(tile_off),
-                projs=projs)
+                projs=projs, tile=tuple(int(t) for t in tile))

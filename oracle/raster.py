@@ -24,8 +24,12 @@ What is computed (per camera, per pixel p = (u, v) at integer coordinates):
 * 2D splat (3DGS, which the paper extends, Sec. 3.4): centre m = (f_x x/z + c_x,
   f_y y/z + c_y) of p_c = R_wc mu + t_wc; covariance J W Sigma W^T J^T + 0.3 I
   with Sigma = R S S^T R^T; alpha = min(0.99, opacity * exp(-1/2 D^T conic D)),
-  D = p - m.  A Gaussian with alpha < 1/255 is skipped; the pixel stops before
-  the first Gaussian that would bring T below 1e-4.
+  D = p - m.  A Gaussian is skipped where alpha < 1/255 or where the pixel
+  lies outside its 3-sigma square |D_x| <= r, |D_y| <= r (r = ceil(3 sqrt of
+  the larger eigenvalue of the 2D covariance), from the float32 binning
+  recipe); the pixel stops before the first Gaussian that would bring T below
+  1e-4.  (3DGS truncates to the tiles the square touches, which makes the
+  image depend on the tile grid; the square itself does not.)
 * Colour: max(0, SH(normalize(mu - C)) . h + 1/2).
 * Compositing (Alg. 2 with T initialised to 1, Eqs. depth_render, t_render,
   semantic_render): w_i = alpha_i T_i; RGB, depth, normal, k and logits are
@@ -45,6 +49,7 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 import torch
 
+from .binning import project_fp32
 from .sh import sh_basis
 
 F64 = torch.float64
@@ -108,6 +113,7 @@ class Prep:
     sem: torch.Tensor      # [N,C]
     z: torch.Tensor        # [N] camera-frame depth of the centre
     sh_raw: torch.Tensor   # [N,3] SH value + 1/2 before the clamp
+    radius: torch.Tensor   # [N] 3-sigma radius r of the float32 recipe (pixels)
 
     def detached_leaves(self) -> "Prep":
         return Prep(*[x.detach().clone().requires_grad_(True)
@@ -146,7 +152,19 @@ def preprocess(p: Params, cam) -> Prep:
     rgb = torch.clamp(sh_raw, min=0.0)
     v_l = torch.einsum("nji,nj->ni", R, C - mu)    # R^T (C - mu)
     v_s = v_l / s
-    return Prep(mean2d, conic, p.opacity, rgb, R, s, v_s, p.kfac, p.sem, z, sh_raw)
+    return Prep(mean2d, conic, p.opacity, rgb, R, s, v_s, p.kfac, p.sem, z, sh_raw,
+                recipe_radius(p, cam))
+
+
+def recipe_radius(p: Params, cam) -> torch.Tensor:
+    """The 3-sigma radius r of the float32 binning recipe (integer-valued) for
+    the (float32-exact) parameters of ``p``; 0 where the recipe culls."""
+    f32 = np.float32
+    sc = dataclasses.make_dataclass("S", ["mean", "quat", "scale", "opacity"])(
+        *[x.detach().numpy().astype(f32) for x in (p.mean, p.quat, p.scale, p.opacity)])
+    pr = project_fp32(sc, cam)
+    r = np.where(pr["valid"], pr["radius"], 0.0)
+    return torch.as_tensor(r.astype(np.float64))
 
 
 def pixel_rays(cam, uv: torch.Tensor):
@@ -199,6 +217,7 @@ def ray_ellipsoid(R: torch.Tensor, s: torch.Tensor, v_s: torch.Tensor,
 
 U32 = 2.0 ** -24          # unit roundoff of float32
 EXP2_APPROX = 2.0 ** -21  # relative error allowed for the hardware exp2 approximation
+SQUARE_BAND = 1e-4        # pixels: |D_x| or |D_y| this close to the 3-sigma radius
 KAPPA_SPLIT = 65.0        # conic eigenvalue ratio above which the kernels evaluate the
                           # quadratic form in double-float (64, plus a margin for their
                           # float32 estimate of the ratio)
@@ -306,8 +325,10 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
         - con[None, :, 1] * dx * dy
     a_raw = op[None, :] * torch.exp(power)
     alpha = torch.clamp(a_raw, max=ALPHA_MAX)
+    rad = prep.radius[ids][None, :]
     with torch.no_grad():
-        valid = alpha >= ALPHA_MIN if frozen is None else frozen[0]
+        in_square = (dx.abs() <= rad) & (dy.abs() <= rad)
+        valid = (alpha >= ALPHA_MIN) & in_square if frozen is None else frozen[0]
     a_eff = torch.where(valid, alpha, torch.zeros_like(alpha))
     one_m = 1.0 - a_eff
     T_after = torch.cumprod(one_m, dim=1)
@@ -357,24 +378,31 @@ def composite_tile(prep: Prep, ids: torch.Tensor, uv: torch.Tensor, cam,
             beta_T = torch.cumsum(step, dim=1)
         else:
             beta_T = torch.full_like(alpha, bands.T)
-        amb_alpha = (evaluated & ((alpha - ALPHA_MIN).abs() <= beta * alpha)).any(1)
+        amb_alpha = (evaluated & in_square & ((alpha - ALPHA_MIN).abs() <= beta * alpha)).any(1)
+        # the 3-sigma square: the kernels form |D| in float32 (error far below
+        # 1e-4 px at these image sizes)
+        near_edge = ((dx.abs() - rad).abs() <= SQUARE_BAND) | ((dy.abs() - rad).abs() <= SQUARE_BAND)
+        amb_square = (evaluated & (alpha >= ALPHA_MIN) & near_edge).any(1)
         amb_T = (evaluated & valid & ((T_after - T_MIN).abs() <= beta_T * T_after)).any(1)
         amb_in = (incl & (qc.abs() <= bands.inside)[None, :]).any(1)
         rel_disc = disc / qa
         amb_disc = (incl & (rel_disc.abs() <= bands.disc)).any(1)
         amb_clamp = (incl & ((a_raw - ALPHA_MAX).abs() <= clamp_w * a_raw)).any(1)
         amb_dg = (incl & (rel_disc.abs() <= bands.disc_grad)).any(1)
-        out["amb_fwd"] = amb_alpha | amb_T | amb_in | amb_disc
+        out["amb_fwd"] = amb_alpha | amb_T | amb_in | amb_disc | amb_square
         out["amb_grad"] = out["amb_fwd"] | amb_clamp | amb_dg
         out["stats_eval"] = evaluated.sum(1)
     return out
 
 
-def tile_pixels(cam, tile_id_local: int, tile: int = 16):
-    TX = (cam.width + tile - 1) // tile
+def tile_pixels(cam, tile_id_local: int, tile=(16, 16)):
+    """Pixel coordinates (u, v) of a camera's tile (row-major tile ids, tiles
+    of tile = (TW, TH) pixels)."""
+    tw, th = (tile, tile) if isinstance(tile, int) else tile
+    TX = (cam.width + tw - 1) // tw
     ty, tx = divmod(tile_id_local, TX)
-    u = np.arange(tx * tile, min((tx + 1) * tile, cam.width))
-    v = np.arange(ty * tile, min((ty + 1) * tile, cam.height))
+    u = np.arange(tx * tw, min((tx + 1) * tw, cam.width))
+    v = np.arange(ty * th, min((ty + 1) * th, cam.height))
     vv, uu = np.meshgrid(v, u, indexing="ij")
     return uu.ravel(), vv.ravel()
 
@@ -388,8 +416,9 @@ def render_camera(prep: Prep, cam, binning, cam_index: int,
     Returns full-size planar images [C,H,W] (pixels of unlisted tiles are 0).
     """
     H, W = cam.height, cam.width
-    TX = (W + 15) // 16
-    TY = (H + 15) // 16
+    tile = tuple(binning.get("tile", (16, 16)))
+    TX = (W + tile[0] - 1) // tile[0]
+    TY = (H + tile[1] - 1) // tile[1]
     C = prep.sem.shape[1]
     off = int(binning["tile_offset"][cam_index])
     ranges = binning["ranges"]
@@ -403,7 +432,7 @@ def render_camera(prep: Prep, cam, binning, cam_index: int,
     for t in tiles:
         s0, s1 = ranges[off + t]
         ids = torch.as_tensor(vals[s0:s1].astype(np.int64))
-        uu, vv = tile_pixels(cam, t)
+        uu, vv = tile_pixels(cam, t, tile)
         uv = torch.as_tensor(np.stack([uu, vv], 1), dtype=F64)
         r = composite_tile(prep, ids, uv, cam, bands, center_depth=center_depth)
         vi = torch.as_tensor(vv)

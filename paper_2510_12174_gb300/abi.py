@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(PKG, "libunigs.so")
 
 UNIGS_MAX_CAMS = 64
 UNIGS_TILE = 16
+UNIGS_TILE_PIXELS = 256
+TILE_SHAPES = ((16, 16), (8, 32), (32, 8), (64, 4))
 UNIGS_MAX_SEM = 64
 UNIGS_FLAG_CENTER_DEPTH = 1
 UNIGS_FLAG_SIMT_LOGITS = 2
@@ -64,7 +66,8 @@ class unigs_config(Structure):
     _fields_ = [("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
                 ("lowpass", c_float), ("step1", c_int32), ("step2", c_int32),
                 ("lambda_", c_float), ("flags", c_uint32), ("batch", c_int32),
-                ("ctas_per_sm", c_int32), ("batch_fwd", c_int32), ("ctas_per_sm_fwd", c_int32)]
+                ("ctas_per_sm", c_int32), ("batch_fwd", c_int32), ("ctas_per_sm_fwd", c_int32),
+                ("tile_w", c_int32), ("tile_h", c_int32)]
 
 
 class unigs_plan(Structure):

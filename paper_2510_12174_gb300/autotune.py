@@ -1,9 +1,12 @@
-"""Launch-shape autotuner for the two composite kernels.
+"""Tile-shape and launch-shape autotuner of the composite kernels.
 
 The composites (forward Alg. 2 and backward Alg. 4) are persistent kernels
-whose CTAs pull 16x16 tiles from a device work counter, longest Gaussian list
-first.  Two launch parameters per kernel change their speed but not their
-results:
+whose CTAs pull tiles of 256 pixels from a device work counter, longest
+Gaussian list first.  The tile shape (16 x 16, 8 x 32, 32 x 8 or 64 x 4)
+decides how many (tile, Gaussian) pairs the binning lists and how well a tile's
+pixels share its Gaussians; it does not change the image (each Gaussian is
+drawn on the pixels of its 3-sigma square, whatever tiles list it).  Two launch
+parameters per kernel change their speed but not their results:
 
 * the batch: Gaussians staged per shared-memory batch (8 - backward only -,
   16, 32 or 64).  Larger
@@ -15,17 +18,17 @@ results:
 The forward output is bit-identical for every shape on the FP32-pipe path
 (each pixel blends its list in the same order) and moves by float32 summation
 order on the tensor-core logit blend; the gradients move by the order of
-float32 atomic additions.  The tile itself stays 16x16 pixels: it is the
-binning unit whose keys and ranges the library reproduces bit for bit, so it
-is not a tuning knob.
+float32 atomic additions.
 
-:func:`tune` times the forward candidates on the forward alone and the
-backward candidates on the backward alone (CUDA events on the caller's scene
-and cameras), keeps the fastest of each, and caches them in a JSON file keyed
+:func:`tune` first times one forward + backward step per tile shape at the
+library's default launch shapes and keeps the fastest shape; at that shape it
+times the forward candidates on the forward alone and the backward candidates
+on the backward alone (CUDA events on the caller's scene and cameras), keeps
+the fastest of each, and caches all three in a JSON file keyed
 by :func:`workload_key` (GPU, SM count, logit class, feature dtype, camera
 count and pixel/Gaussian magnitudes), so a training run pays the search once
 per workload class.  :func:`config_for` returns a ``unigs_config`` with the
-cached shapes (or the library defaults).
+cached tile and launch shapes (or the library defaults).
 """
 from __future__ import annotations
 
@@ -39,6 +42,7 @@ import torch
 from . import abi
 from . import rasterizer as rz
 
+TILE_CANDIDATES: Tuple[Tuple[int, int], ...] = tuple(abi.TILE_SHAPES)
 FWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 4), (16, 3), (32, 2), (16, 2), (64, 2))
 BWD_CANDIDATES: Tuple[Tuple[int, int], ...] = ((8, 3), (32, 2), (16, 2), (8, 2), (64, 1))
 
@@ -100,11 +104,13 @@ def _store(path: str, key: str, entry: dict) -> None:
 
 
 def make_config(batch: int = 0, ctas_per_sm: int = 0, base: Optional[abi.unigs_config] = None,
-                batch_fwd: int = 0, ctas_per_sm_fwd: int = 0):
+                batch_fwd: int = 0, ctas_per_sm_fwd: int = 0, tile=None):
     cfg = (abi.unigs_config.from_buffer_copy(base) if base is not None
            else abi.unigs_config_default())
     cfg.batch, cfg.ctas_per_sm = int(batch), int(ctas_per_sm)
     cfg.batch_fwd, cfg.ctas_per_sm_fwd = int(batch_fwd), int(ctas_per_sm_fwd)
+    if tile is not None:
+        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
     return cfg
 
 
@@ -131,14 +137,36 @@ def _median_ms(fn, stream, reps: int) -> float:
     return times[len(times) // 2]
 
 
+def time_tile(scene, cams, tile, reps: int = 3, base: Optional[abi.unigs_config] = None,
+              seed: int = 0) -> float:
+    """Milliseconds of one forward + backward step (preprocess, binning,
+    forward composite, backward) at the tile shape and the default launch
+    shapes, median of ``reps`` after one warm-up."""
+    r = rz.Renderer(scene, cams, cfg=make_config(0, 0, base, 0, 0, tile))
+    out = r.forward()                       # sizes the instance capacity
+    stream = torch.cuda.current_stream(r.device)
+    up = _synthetic_upstream(r, seed)
+    grads = r.alloc_grads()
+
+    def step():
+        r.forward(out, readback=False, normal_d=False)
+        r.backward(out, up, grads=grads)
+
+    step()
+    ms = _median_ms(step, stream, reps)
+    s, _ = r.status()
+    abi.check(s, f"tile shape {tile}")
+    return ms
+
+
 def time_shape(scene, cams, batch: int, ctas_per_sm: int, reps: int = 3,
                base: Optional[abi.unigs_config] = None, seed: int = 0,
-               stage: str = "bwd") -> float:
+               stage: str = "bwd", tile=None) -> float:
     """Milliseconds of the forward composite (stage "fwd": preprocess, sort
     and forward at the shape) or of the backward (stage "bwd"), median of
     ``reps`` after one warm-up."""
-    cfg = (make_config(0, 0, base, batch, ctas_per_sm) if stage == "fwd"
-           else make_config(batch, ctas_per_sm, base))
+    cfg = (make_config(0, 0, base, batch, ctas_per_sm, tile) if stage == "fwd"
+           else make_config(batch, ctas_per_sm, base, tile=tile))
     r = rz.Renderer(scene, cams, cfg=cfg)
     out = r.forward()                       # sizes the instance capacity
     stream = torch.cuda.current_stream(r.device)
@@ -157,17 +185,48 @@ def time_shape(scene, cams, batch: int, ctas_per_sm: int, reps: int = 3,
 def tune(scene, cams, fwd_candidates: Iterable[Tuple[int, int]] = FWD_CANDIDATES,
          bwd_candidates: Iterable[Tuple[int, int]] = BWD_CANDIDATES, reps: int = 3,
          base: Optional[abi.unigs_config] = None, cache_path: Optional[str] = None,
-         force: bool = False, timer=None) -> Dict[str, Tuple[int, int]]:
-    """Fastest forward and backward (batch, ctas_per_sm) for this scene and
-    camera set, cached: {"fwd": (b, c), "bwd": (b, c)}.
+         force: bool = False, timer=None,
+         tile_candidates: Iterable[Tuple[int, int]] = TILE_CANDIDATES,
+         tile_timer=None) -> Dict[str, Tuple[int, int]]:
+    """Fastest tile shape, then the fastest forward and backward (batch,
+    ctas_per_sm) at that tile, for this scene and camera set, cached:
+    {"tile": (w, h), "fwd": (b, c), "bwd": (b, c)}.
 
-    ``timer(stage, batch, ctas_per_sm) -> ms`` replaces the CUDA-event timing
-    of :func:`time_shape`."""
+    ``tile_timer(tile) -> ms`` and ``timer(stage, batch, ctas_per_sm) -> ms``
+    replace the CUDA-event timings of :func:`time_tile` and
+    :func:`time_shape`."""
     path = cache_path or default_cache_path()
     key = workload_key(scene, cams)
-    t = timer or (lambda st, b, c: time_shape(scene, cams, b, c, reps=reps, base=base, stage=st))
-    return {"fwd": search(key, "fwd", fwd_candidates, path, force, lambda b, c: t("fwd", b, c)),
+    tt = tile_timer or (lambda tl: time_tile(scene, cams, tl, reps=reps, base=base))
+    tile = search_tile(key, tile_candidates, path, force, tt)
+    t = timer or (lambda st, b, c: time_shape(scene, cams, b, c, reps=reps, base=base, stage=st,
+                                              tile=tile))
+    return {"tile": tile,
+            "fwd": search(key, "fwd", fwd_candidates, path, force, lambda b, c: t("fwd", b, c)),
             "bwd": search(key, "bwd", bwd_candidates, path, force, lambda b, c: t("bwd", b, c))}
+
+
+def search_tile(key: str, candidates: Iterable[Tuple[int, int]], path: str, force: bool,
+                timer) -> Tuple[int, int]:
+    """Cache lookup of the tile shape of ``key``, else time every candidate
+    and store the fastest."""
+    if not force:
+        hit = _load(path).get(key, {}).get("tile")
+        if hit:
+            return int(hit["w"]), int(hit["h"])
+    results = {}
+    for w, h in candidates:
+        if (int(w), int(h)) not in abi.TILE_SHAPES:
+            raise ValueError(f"invalid tile shape ({w}, {h})")
+        results[f"{w}x{h}"] = float(timer((int(w), int(h))))
+    if not results:
+        raise ValueError("no tile shape to try")
+    best = min(results, key=results.get)
+    w, h = (int(x) for x in best.split("x"))
+    entry = _load(path).get(key, {})
+    entry["tile"] = {"w": w, "h": h, "ms": results}
+    _store(path, key, entry)
+    return w, h
 
 
 def search(key: str, slot: str, candidates: Iterable[Tuple[int, int]], path: str, force: bool,
@@ -200,12 +259,13 @@ def config_for(scene, cams, base: Optional[abi.unigs_config] = None,
     ``tune_if_missing``)."""
     path = cache_path or default_cache_path()
     hit = _load(path).get(workload_key(scene, cams), {})
-    if tune_if_missing and not ("fwd" in hit and "bwd" in hit):
+    if tune_if_missing and not ("fwd" in hit and "bwd" in hit and "tile" in hit):
         tune(scene, cams, base=base, cache_path=path)
         hit = _load(path).get(workload_key(scene, cams), {})
-    f, b = hit.get("fwd", {}), hit.get("bwd", {})
+    f, b, tl = hit.get("fwd", {}), hit.get("bwd", {}), hit.get("tile")
     return make_config(b.get("batch", 0), b.get("ctas_per_sm", 0), base,
-                       f.get("batch", 0), f.get("ctas_per_sm", 0))
+                       f.get("batch", 0), f.get("ctas_per_sm", 0),
+                       (tl["w"], tl["h"]) if tl else None)
 
 
 def main(argv=None):
@@ -228,6 +288,7 @@ def main(argv=None):
     best = tune(ds, cams, reps=args.reps, cache_path=path, force=True)
     entry = _load(path).get(workload_key(ds, cams), {})
     print(json.dumps({"workload": workload_key(ds, cams), "best": best,
+                      "tile_ms": entry.get("tile", {}).get("ms"),
                       "fwd_ms": entry.get("fwd", {}).get("ms"),
                       "bwd_ms": entry.get("bwd", {}).get("ms")}, indent=1))
 

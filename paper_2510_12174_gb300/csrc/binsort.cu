@@ -115,7 +115,8 @@ int scan_u32(const uint32_t* in, int64_t n, uint32_t* partial, uint32_t* out, ui
 // (key, value) per overlapped tile in (camera, Gaussian, tile row-major)
 // order.
 __global__ void __launch_bounds__(256)
-    emit_kernel(const CamTable* __restrict__ tab, int64_t n, int n_cams, int64_t capacity,
+    emit_kernel(const CamTable* __restrict__ tab, int64_t n, int n_cams, int tw, int th,
+                int64_t capacity,
                 const uint2* __restrict__ rect, const uint32_t* __restrict__ touched,
                 const uint32_t* __restrict__ offs, const uint32_t* __restrict__ zbits,
                 const float* __restrict__ cull, WsHeader* __restrict__ hdr,
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(256)
             const uint32_t o_end = o + cnt;
             for (int ty = y0; ty < y1; ++ty)
                 for (int tx = x0; tx < x1; ++tx) {
-                    if (!tile_keep(cr, tx, ty) || o >= o_end) continue;
+                    if (!tile_keep(cr, tx, ty, tw, th) || o >= o_end) continue;
                     const unsigned long long tile = toff + (unsigned long long)(ty * tiles_x + tx);
                     keys[o] = (tile << 32) | zb;
                     vals[o] = g;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(256)
             for (int j0 = 0; j0 < bn; j0 += 32) {
                 const int j = j0 + lane;
                 const int tx = bx0 + j % bw, ty = by0 + j / bw;
-                const bool keep = j < bn && tile_keep(cb, tx, ty);
+                const bool keep = j < bn && tile_keep(cb, tx, ty, tw, th);
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 const uint32_t dst = bo + __popc(m & lt_mask);
                 if (keep && dst < bend) {
@@ -363,7 +364,7 @@ int launch_bin_sort(const unigs_plan& p, void* ws, cudaStream_t st) {
         const int64_t blocks = (total + 255) / 256;
         const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
         emit_kernel<<<grid, 256, 0, st>>>(ws_ptr<CamTable>(ws, p, OFF_CAM), p.n, p.n_cams,
-                                          p.capacity, ws_ptr<uint2>(ws, p, OFF_RECT), touched,
+                                          p.cfg.tile_w, p.cfg.tile_h, p.capacity, ws_ptr<uint2>(ws, p, OFF_RECT), touched,
                                           offs, ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
                                           ws_ptr<float>(ws, p, OFF_CULL), hdr, keys[0], vals[0]);
         ++launches;

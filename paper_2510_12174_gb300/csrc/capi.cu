@@ -58,8 +58,11 @@ bool build_cam_table(const unigs_plan* p, const unigs_camera* cams, CamTable* ta
         DevCam& d = tab->cam[k];
         d.width = c.width;
         d.height = c.height;
-        d.tiles_x = (c.width + TILE - 1) / TILE;
-        d.tiles_y = (c.height + TILE - 1) / TILE;
+        const int tw = p->cfg.tile_w, th = p->cfg.tile_h;
+        d.tiles_x = (c.width + tw - 1) / tw;
+        d.tiles_y = (c.height + th - 1) / th;
+        d.tile_w = tw;
+        d.tile_h = th;
         d.tile_off = p->tile_offset[k];
         d.pix_off = p->pixel_offset[k];
         d.fx = c.fx;
@@ -116,6 +119,8 @@ void unigs_config_default(unigs_config* cfg) {
     cfg->ctas_per_sm = 0;
     cfg->batch_fwd = 0;
     cfg->ctas_per_sm_fwd = 0;
+    cfg->tile_w = 0;
+    cfg->tile_h = 0;
 }
 
 unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const unigs_camera* cams,
@@ -153,6 +158,15 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
         return UNIGS_ERR_INVALID_ARG;
     if (plan->cfg.ctas_per_sm_fwd < 0 || plan->cfg.ctas_per_sm_fwd > 8)
         return UNIGS_ERR_INVALID_ARG;
+    if (plan->cfg.tile_w == 0 && plan->cfg.tile_h == 0) plan->cfg.tile_w = plan->cfg.tile_h = TILE;
+    {
+        // 256 pixels per tile (one per composite thread), rows of whole 8x4
+        // warp blocks
+        const int tw = plan->cfg.tile_w, th = plan->cfg.tile_h;
+        if (!((tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8) ||
+              (tw == 64 && th == 4)))
+            return UNIGS_ERR_INVALID_ARG;
+    }
     plan->n = g->n;
     plan->n_cams = n_cams;
     plan->n_sem = g->n_sem;
@@ -166,7 +180,8 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
         if (!(c.fx > 0.f) || !(c.fy > 0.f)) return UNIGS_ERR_INVALID_ARG;
         plan->tile_offset[k] = (int32_t)tiles;
         plan->pixel_offset[k] = pixels;
-        tiles += (int64_t)((c.width + TILE - 1) / TILE) * ((c.height + TILE - 1) / TILE);
+        tiles += (int64_t)((c.width + plan->cfg.tile_w - 1) / plan->cfg.tile_w) *
+                 ((c.height + plan->cfg.tile_h - 1) / plan->cfg.tile_h);
         pixels += (int64_t)c.width * c.height;
     }
     if (tiles > 0x7fffffffLL) return UNIGS_ERR_INVALID_ARG;

@@ -20,8 +20,16 @@ namespace unigs {
 
 constexpr int MAX_STEP = 4;
 
+// The normal-from-depth kernels work on blocks of DN_TILE x DN_TILE pixels
+// of their own (independent of the binning tile shape): block b of the launch
+// belongs to the camera k with blk_off[k] <= b < blk_off[k + 1] and is block
+// b - blk_off[k] of that camera, row-major with blk_x[k] blocks per row.
+constexpr int DN_TILE = 16;
+
 struct DNParams {
     CamTable tab;  // by value: these entry points take no workspace
+    int32_t blk_off[UNIGS_MAX_CAMS + 1];
+    int32_t blk_x[UNIGS_MAX_CAMS];
     int n_cams;
     int step1, step2;
     float lambda;
@@ -31,6 +39,14 @@ struct DNParams {
     const float* g_depth_in;
     float* g_depth_out;
 };
+
+// The camera whose blocks contain blockIdx.x.
+__device__ __forceinline__ void dn_block(const DNParams& P, int* k) {
+    int c = 0;
+    for (int j = 1; j < P.n_cams; ++j)
+        if ((int)blockIdx.x >= P.blk_off[j]) c = j;
+    *k = c;
+}
 
 // Camera-frame difference of two back-projected points along x or y.
 __device__ __forceinline__ void diff_x(float xt_p, float yt, float Dp, float Dm, float two_g_fx,
@@ -95,11 +111,12 @@ __device__ __forceinline__ bool dn_forward(const DevCam& cam, int u, int v, int 
 }
 
 __global__ void __launch_bounds__(256) depth_normal_fwd_kernel(const __grid_constant__ DNParams P) {
-    int cam_idx;
-    const DevCam& cam = cam_of_tile(&P.tab, P.n_cams, blockIdx.x, &cam_idx);
-    const int64_t lt = blockIdx.x - cam.tile_off;
-    const int u = (int)(lt % cam.tiles_x) * TILE + (threadIdx.x & 15);
-    const int v = (int)(lt / cam.tiles_x) * TILE + (threadIdx.x >> 4);
+    int k = 0;
+    dn_block(P, &k);
+    const DevCam& cam = P.tab.cam[k];
+    const int lt = (int)blockIdx.x - P.blk_off[k];
+    const int u = (lt % P.blk_x[k]) * DN_TILE + (threadIdx.x & 15);
+    const int v = (lt / P.blk_x[k]) * DN_TILE + (threadIdx.x >> 4);
     if (u >= cam.width || v >= cam.height) return;
     const int W = cam.width;
     const int64_t HW = (int64_t)cam.height * W;
@@ -124,18 +141,19 @@ __global__ void __launch_bounds__(256) depth_normal_fwd_kernel(const __grid_cons
 // pixel q of the tile plus a halo of smax the gradients w.r.t. its four
 // difference vectors (vx1, vy1, vx2, vy2), camera frame.
 __global__ void __launch_bounds__(256) depth_normal_bwd_kernel(const __grid_constant__ DNParams P) {
-    constexpr int DP_MAX = TILE + 4 * MAX_STEP;  // depth tile pitch
-    constexpr int GP_MAX = TILE + 2 * MAX_STEP;  // gradient tile pitch
+    constexpr int DP_MAX = DN_TILE + 4 * MAX_STEP;  // depth tile pitch
+    constexpr int GP_MAX = DN_TILE + 2 * MAX_STEP;  // gradient tile pitch
     __shared__ float sD[DP_MAX * DP_MAX];
     __shared__ float sG[GP_MAX * GP_MAX][12];
-    int cam_idx;
-    const DevCam& cam = cam_of_tile(&P.tab, P.n_cams, blockIdx.x, &cam_idx);
-    const int64_t lt = blockIdx.x - cam.tile_off;
-    const int u0 = (int)(lt % cam.tiles_x) * TILE, v0 = (int)(lt / cam.tiles_x) * TILE;
+    int k = 0;
+    dn_block(P, &k);
+    const DevCam& cam = P.tab.cam[k];
+    const int lt = (int)blockIdx.x - P.blk_off[k];
+    const int u0 = (lt % P.blk_x[k]) * DN_TILE, v0 = (lt / P.blk_x[k]) * DN_TILE;
     const int W = cam.width, H = cam.height;
     const int64_t HW = (int64_t)H * W;
     const int h = max(P.step1, P.step2);
-    const int dp = TILE + 4 * h, gp = TILE + 2 * h;
+    const int dp = DN_TILE + 4 * h, gp = DN_TILE + 2 * h;
     const float* Dimg = P.depth + cam.pix_off;
     const float* gN = P.g_normal + cam.pix_off * 3;
 
@@ -210,6 +228,13 @@ __global__ void __launch_bounds__(256) depth_normal_bwd_kernel(const __grid_cons
 static void make_dn(const unigs_plan& p, const CamTable& tab, DNParams& P) {
     P.tab = tab;
     P.n_cams = p.n_cams;
+    int32_t off = 0;
+    for (int k = 0; k < p.n_cams; ++k) {
+        P.blk_off[k] = off;
+        P.blk_x[k] = (tab.cam[k].width + DN_TILE - 1) / DN_TILE;
+        off += P.blk_x[k] * ((tab.cam[k].height + DN_TILE - 1) / DN_TILE);
+    }
+    P.blk_off[p.n_cams] = off;
     P.step1 = p.cfg.step1;
     P.step2 = p.cfg.step2;
     P.lambda = p.cfg.lambda;
@@ -225,7 +250,7 @@ int launch_depth_normal_fwd(const unigs_plan& p, const CamTable& tab, const floa
     P.g_normal = nullptr;
     P.g_depth_in = nullptr;
     P.g_depth_out = nullptr;
-    depth_normal_fwd_kernel<<<(unsigned)p.n_tiles, 256, 0, st>>>(P);
+    depth_normal_fwd_kernel<<<(unsigned)P.blk_off[p.n_cams], 256, 0, st>>>(P);
     return 1;
 }
 
@@ -240,7 +265,7 @@ int launch_depth_normal_bwd(const unigs_plan& p, const CamTable& tab, const floa
     P.g_normal = g_normal_d;
     P.g_depth_in = g_depth_in;
     P.g_depth_out = g_depth_out;
-    depth_normal_bwd_kernel<<<(unsigned)p.n_tiles, 256, 0, st>>>(P);
+    depth_normal_bwd_kernel<<<(unsigned)P.blk_off[p.n_cams], 256, 0, st>>>(P);
     return 1;
 }
 

@@ -35,10 +35,11 @@ struct Recipe {
     bool valid;
 };
 
-__device__ __forceinline__ void rect_axis(float m, float r, int n_tiles, int* lo, int* hi) {
+__device__ __forceinline__ void rect_axis(float m, float r, int n_tiles, int side, int* lo,
+                                          int* hi) {
     const float nt = (float)n_tiles;
-    float l = floorf(__fdiv_rn(RS(m, r), (float)TILE));
-    float h = ceilf(__fdiv_rn(RA(m, r), (float)TILE));
+    float l = floorf(__fdiv_rn(RS(m, r), (float)side));
+    float h = ceilf(__fdiv_rn(RA(m, r), (float)side));
     l = fminf(fmaxf(l, 0.f), nt);
     h = fminf(fmaxf(h, 0.f), nt);
     *lo = (int)l;
@@ -116,8 +117,8 @@ __device__ __forceinline__ void binning_recipe(const DevCam& cam, float mx_, flo
     o.radius = ceilf(RM(3.f, __fsqrt_rn(lam)));
     o.mx = RA(RM(cam.fx, xz), cam.cx);
     o.my = RA(RM(cam.fy, yz), cam.cy);
-    rect_axis(o.mx, o.radius, cam.tiles_x, &o.x0, &o.x1);
-    rect_axis(o.my, o.radius, cam.tiles_y, &o.y0, &o.y1);
+    rect_axis(o.mx, o.radius, cam.tiles_x, cam.tile_w, &o.x0, &o.x1);
+    rect_axis(o.my, o.radius, cam.tiles_y, cam.tile_h, &o.y0, &o.y1);
     o.valid = in_front && qok && det_ok && (o.x1 > o.x0) && (o.y1 > o.y0);
 }
 
@@ -236,19 +237,21 @@ __device__ __forceinline__ void cull_record(const Recipe& rc, float op, float* c
     cr[7] = 0.f;
 }
 
-// Number of kept tiles of the rectangle [x0,x1) x [y0,y1) (opacity-aware test).
+// Number of kept tiles of the rectangle [x0,x1) x [y0,y1) (opacity-aware test)
+// for tiles of tw x th pixels.
 __device__ __forceinline__ uint32_t count_kept_serial(const float* cr, int x0, int x1, int y0,
-                                                      int y1) {
+                                                      int y1, int tw, int th) {
     uint32_t kept = 0;
     for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) kept += tile_keep(cr, tx, ty) ? 1u : 0u;
+        for (int tx = x0; tx < x1; ++tx) kept += tile_keep(cr, tx, ty, tw, th) ? 1u : 0u;
     return kept;
 }
 
 
 __global__ void __launch_bounds__(256)
     preprocess_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab, int n_cams,
-                      float lowpass, float* __restrict__ rec, uint2* __restrict__ rect,
+                      int tw, int th, float lowpass, float* __restrict__ rec,
+                      uint2* __restrict__ rect,
                       uint32_t* __restrict__ touched, uint32_t* __restrict__ zbits,
                       float* __restrict__ cull) {
     const int64_t n = g.n;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(256)
             }
         }
         uint32_t kept = (nt > 0 && nt <= COOP_TILES)
-                            ? count_kept_serial(cr, rc.x0, rc.x1, rc.y0, rc.y1) : 0u;
+                            ? count_kept_serial(cr, rc.x0, rc.x1, rc.y0, rc.y1, tw, th) : 0u;
         unsigned big = __ballot_sync(0xffffffffu, nt > COOP_TILES);
         while (big) {
             const int src = __ffs(big) - 1;
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256)
             uint32_t cnt = 0;
             for (int j0 = 0; j0 < bn; j0 += 32) {
                 const int j = j0 + lane;
-                const bool keep = j < bn && tile_keep(cb, bx0 + j % bw, by0 + j / bw);
+                const bool keep = j < bn && tile_keep(cb, bx0 + j % bw, by0 + j / bw, tw, th);
                 cnt += __popc(__ballot_sync(0xffffffffu, keep));
             }
             if (lane == src) kept = cnt;
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(256)
                 o[R_P1 + a] = kap[a] * fmaf(Ma[2], mty, -Ma[1]) * ifx;
                 o[R_P2 + a] = kap[a] * fmaf(-Ma[2], mtx, Ma[0]) * ify;
             }
-            o[R_PAD] = 0.f;
+            o[R_R3] = rc.radius;
         }
         {
             const float* v = o + R_VS;
@@ -491,7 +494,8 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
         const int64_t blocks = (total + 255) / 256;
         const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
         preprocess_kernel<<<grid, 256, 0, st>>>(
-            g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.n_cams, p.cfg.lowpass,
+            g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.n_cams, p.cfg.tile_w, p.cfg.tile_h,
+            p.cfg.lowpass,
             ws_ptr<float>(ws, p, OFF_REC), ws_ptr<uint2>(ws, p, OFF_RECT),
             ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
             ws_ptr<float>(ws, p, OFF_CULL));

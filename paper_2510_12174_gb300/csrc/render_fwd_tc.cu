@@ -159,10 +159,14 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
         const int64_t ltile = gtile - cam.tile_off;
         const int tx = (int)(ltile % cam.tiles_x), ty = (int)(ltile / cam.tiles_x);
         int lx, ly;
-        tile_pixel(tid, &lx, &ly);
-        const int u = tx * TILE + lx, v = ty * TILE + ly;
-        const float bx0 = (float)(tx * TILE + (warp & 1) * 8);
-        const float by0 = (float)(ty * TILE + (warp >> 1) * 4);
+        const int tw = cam.tile_w, th = cam.tile_h;
+        tile_pixel(tid, tw, &lx, &ly);
+        const int u = tx * tw + lx, v = ty * th + ly;
+        // the warp's 8x4 pixel block, for the per-warp bounding-box skip
+        int wbx, wby;
+        warp_block(warp, tw, &wbx, &wby);
+        const float bx0 = (float)(tx * tw + wbx);
+        const float by0 = (float)(ty * th + wby);
         const bool inside = u < cam.width && v < cam.height;
         const float uf = (float)u, vf = (float)v;
         const float xt = (uf - cam.cx) / cam.fx, yt = (vf - cam.cy) / cam.fy;

@@ -7,37 +7,49 @@
 namespace unigs {
 
 // alpha = min(alpha_max, opacity * exp(-1/2 D^T conic D)), D = pixel - centre,
-// with the centre held as integer part + remainder.  Ill-conditioned splats
-// (flag set by the preprocess) evaluate the quadratic form in double-float
-// from the double-float conic; the branch is uniform across a CTA because all
-// its threads walk the same Gaussian.  Written with non-contractible
-// intrinsics so the forward and the backward (which recomputes alpha to undo
-// T) obtain the same bits.
+// with the centre held as integer part + remainder.  A pixel outside the
+// Gaussian's 3-sigma square (|D_x| > r or |D_y| > r, r of the binning recipe)
+// gets -1, below every alpha_min: the Gaussian is not drawn there (the tiles
+// of the binning only have to cover the square, so the image does not depend
+// on the tile shape).  Ill-conditioned splats (flag set by the preprocess)
+// evaluate the quadratic form in double-float from the double-float conic;
+// the branch is uniform across a CTA because all its threads walk the same
+// Gaussian.  Written with non-contractible intrinsics so the forward and the
+// backward (which recomputes alpha to undo T) obtain the same bits.
 __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float uf, float vf,
                                              float alpha_max, float* dx_out, float* dy_out,
                                              float* gauss_out) {
     const float ux = __fsub_rn(uf, rc[R_MXH]);  // exact (integers)
     const float vy = __fsub_rn(vf, rc[R_MYH]);
+    const float r3 = rc[R_R3];
     float q;
     if (rc[R_FLAG] != 0.f) {
         const ff dx = two_sum(ux, -rc[R_MXL]);
         const ff dy = two_sum(vy, -rc[R_MYL]);
+        *dx_out = ff_val(dx);
+        *dy_out = ff_val(dy);
+        if (fabsf(*dx_out) > r3 || fabsf(*dy_out) > r3) {
+            *gauss_out = 0.f;
+            return -1.f;
+        }
         const ff A = {rc[R_CON], rc[R_CLO]}, B = {rc[R_CON + 1], rc[R_CLO + 1]},
                  C = {rc[R_CON + 2], rc[R_CLO + 2]};
         const ff t1 = ff_mul(A, ff_mul(dx, dx));
         const ff t2 = ff_scale(ff_mul(B, ff_mul(dx, dy)), 2.f);
         const ff t3 = ff_mul(C, ff_mul(dy, dy));
         q = ff_val(ff_add(ff_add(t1, t2), t3));
-        *dx_out = ff_val(dx);
-        *dy_out = ff_val(dy);
     } else {
         const float dx = __fsub_rn(ux, rc[R_MXL]);
         const float dy = __fsub_rn(vy, rc[R_MYL]);
+        *dx_out = dx;
+        *dy_out = dy;
+        if (fabsf(dx) > r3 || fabsf(dy) > r3) {
+            *gauss_out = 0.f;
+            return -1.f;
+        }
         const float A = rc[R_CON], B = rc[R_CON + 1], C = rc[R_CON + 2];
         q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(C, dy), dy)),
                       __fmul_rn(2.f, __fmul_rn(__fmul_rn(B, dx), dy)));
-        *dx_out = dx;
-        *dy_out = dy;
     }
     const float G = __expf(__fmul_rn(-0.5f, q));
     *gauss_out = G;

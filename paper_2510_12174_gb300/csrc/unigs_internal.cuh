@@ -9,8 +9,8 @@
 
 namespace unigs {
 
-constexpr int TILE = UNIGS_TILE;
-constexpr int TILE_PIX = TILE * TILE;
+constexpr int TILE = UNIGS_TILE;             // default tile side
+constexpr int TILE_PIX = UNIGS_TILE_PIXELS;  // pixels of every tile shape
 
 // ----------------------------------------------------------------------------
 // Per-(camera, Gaussian) forward record written by the preprocess and staged
@@ -40,20 +40,30 @@ constexpr int TILE_PIX = TILE * TILE;
 //           (dx, dy) from the projected centre (see pair_geometry), the
 //           cancellation-free form of the cross product for Gaussians far
 //           from the camera
-//   [47]    unused (keeps the record a whole number of 16-byte words)
+//   [47]    3-sigma radius r of the binning recipe (pixels): the Gaussian is
+//           drawn only where |dx| <= r and |dy| <= r
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_CON = 4, R_OP = 7, R_EXTX = 8, R_EXTY = 9,
     R_FLAG = 10, R_SR = 11, R_MC = 12, R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34,
-    R_K = 37, R_RGB = 38, R_P1 = 41, R_P2 = 44, R_PAD = 47, REC_FLOATS = 48
+    R_K = 37, R_RGB = 38, R_P1 = 41, R_P2 = 44, R_R3 = 47, REC_FLOATS = 48
 };
 
-// Pixel of thread tid inside its 16x16 tile: warp w covers the 8x4 block at
-// ((w & 1) * 8, (w >> 1) * 4), lanes row-major within the block.
-__device__ __forceinline__ void tile_pixel(int tid, int* lx, int* ly) {
-    const int w = tid >> 5, lane = tid & 31;
-    *lx = (w & 1) * 8 + (lane & 7);
-    *ly = (w >> 1) * 4 + (lane >> 3);
+// Pixel of thread tid inside its tile of width tw (8, 16, 32 or 64; 256
+// pixels): the tile is a grid of 8x4 warp blocks, tw / 8 per row; warp w
+// covers the block at ((w % (tw/8)) * 8, (w / (tw/8)) * 4), lanes row-major
+// within the block.
+__device__ __forceinline__ void tile_pixel(int tid, int tw, int* lx, int* ly) {
+    const int w = tid >> 5, lane = tid & 31, wpr = tw >> 3;
+    *lx = (w % wpr) * 8 + (lane & 7);
+    *ly = (w / wpr) * 4 + (lane >> 3);
+}
+
+// Origin of warp w's 8x4 block inside a tile of width tw.
+__device__ __forceinline__ void warp_block(int w, int tw, int* bx, int* by) {
+    const int wpr = tw >> 3;
+    *bx = (w % wpr) * 8;
+    *by = (w / wpr) * 4;
 }
 
 // True when the Gaussian cannot reach alpha_min anywhere in the warp's block
@@ -92,7 +102,8 @@ struct DevCam {
     float R_cw[9];
     float C[3];
     float z_near;
-    float pad[3];
+    int32_t tile_w, tile_h;  // tile shape of the plan (the same for every camera)
+    float pad;
 };
 static_assert(sizeof(DevCam) == 160, "DevCam layout");
 
@@ -134,11 +145,12 @@ __device__ __forceinline__ float cull_q(float kA, float kB, float kC, float dx, 
                      __fmul_rn(__fmul_rn(kC, dy), dy));
 }
 
-__device__ __forceinline__ bool tile_keep(const float* __restrict__ cr, int tx, int ty) {
+__device__ __forceinline__ bool tile_keep(const float* __restrict__ cr, int tx, int ty, int tw,
+                                          int th) {
     if (cr[C_NOCULL] != 0.f) return true;
     const float mx = cr[C_MX], my = cr[C_MY], kA = cr[C_KA], kB = cr[C_KB], kC = cr[C_KC];
-    const float X0 = (float)(tx * TILE), X1 = (float)(tx * TILE + TILE - 1);
-    const float Y0 = (float)(ty * TILE), Y1 = (float)(ty * TILE + TILE - 1);
+    const float X0 = (float)(tx * tw), X1 = (float)(tx * tw + tw - 1);
+    const float Y0 = (float)(ty * th), Y1 = (float)(ty * th + th - 1);
     float qmin;
     if (X0 <= mx && mx <= X1 && Y0 <= my && my <= Y1) {
         qmin = 0.f;

@@ -52,6 +52,48 @@ def test_search_rejects_invalid_shapes(tmp_path):
                         lambda b, c: 1.0)
 
 
+def test_tile_search_picks_fastest_and_caches(tmp_path):
+    path = str(tmp_path / "shapes.json")
+    cost = {(16, 16): 5.0, (32, 8): 4.0, (8, 32): 6.0, (64, 4): 4.5}
+    calls = []
+
+    def timer(tile):
+        calls.append(tile)
+        return cost[tile]
+
+    assert autotune.search_tile("k", cost, path, False, timer) == (32, 8)
+    assert len(calls) == 4
+    assert autotune.search_tile("k", cost, path, False, timer) == (32, 8)
+    assert len(calls) == 4
+    d = json.load(open(path))
+    assert d["k"]["tile"] == {"w": 32, "h": 8, "ms": {"16x16": 5.0, "32x8": 4.0, "8x32": 6.0,
+                                                      "64x4": 4.5}}
+    with pytest.raises(ValueError):
+        autotune.search_tile("k2", [(16, 8)], path, False, timer)
+
+
+def test_tune_chooses_tile_then_launch_shapes(tmp_path):
+    path = str(tmp_path / "shapes.json")
+    seen = []
+
+    def tile_timer(tile):
+        return {(16, 16): 3.0, (32, 8): 2.0}[tile]
+
+    def timer(stage, b, c):
+        seen.append((stage, b, c))
+        return float(b * c)
+
+    import paper_2510_12174_gb300.autotune as at
+    key = at.key_for("G", 1, 16, "bf16", [(64, 48)], 4000)
+    # workload_key needs a device: exercise the same steps with the key
+    tile = at.search_tile(key, [(16, 16), (32, 8)], path, False, tile_timer)
+    fwd = at.search(key, "fwd", [(16, 4), (32, 2)], path, False, lambda b, c: timer("fwd", b, c))
+    bwd = at.search(key, "bwd", [(8, 3), (16, 1)], path, False, lambda b, c: timer("bwd", b, c))
+    assert tile == (32, 8) and fwd == (16, 4) and bwd == (16, 1)
+    d = json.load(open(path))[key]
+    assert set(d) == {"tile", "fwd", "bwd"}
+
+
 def test_corrupt_cache_is_ignored(tmp_path):
     path = tmp_path / "s.json"
     path.write_text("{not json")
@@ -69,9 +111,12 @@ def test_tune_on_small_scene(tmp_path):
     ds = rz.DeviceScene.from_scene(sc)
     path = str(tmp_path / "s.json")
     best = autotune.tune(ds, cams, fwd_candidates=[(16, 4), (32, 2)],
-                         bwd_candidates=[(32, 2), (16, 1)], reps=2, cache_path=path)
+                         bwd_candidates=[(32, 2), (16, 1)], reps=2, cache_path=path,
+                         tile_candidates=[(16, 16), (32, 8)])
+    assert best["tile"] in [(16, 16), (32, 8)]
     assert best["fwd"] in [(16, 4), (32, 2)] and best["bwd"] in [(32, 2), (16, 1)]
     cfg = autotune.config_for(ds, cams, cache_path=path)
     assert (cfg.batch, cfg.ctas_per_sm) == best["bwd"]
     assert (cfg.batch_fwd, cfg.ctas_per_sm_fwd) == best["fwd"]
+    assert (cfg.tile_w, cfg.tile_h) == best["tile"]
     torch.cuda.synchronize()

@@ -301,14 +301,15 @@ def test_fp32_recipe_tracks_fp64_projection():
     assert np.all(3 * np.sqrt(cov[:, 2]) <= r + 1e-6)
 
 
-def _keep_scalar(pr, g, tx, ty):
+def _keep_scalar(pr, g, tx, ty, tile=(16, 16)):
     """The opacity-aware tile test written out with float32 scalars."""
     f = np.float32
     if pr["no_cull"][g]:
         return True
     mx, my = f(pr["mean2d"][0][g]), f(pr["mean2d"][1][g])
     kA, kB, kC = (f(pr["conic32"][i][g]) for i in range(3))
-    X0, X1, Y0, Y1 = f(16 * tx), f(16 * tx + 15), f(16 * ty), f(16 * ty + 15)
+    tw, th = tile
+    X0, X1, Y0, Y1 = f(tw * tx), f(tw * tx + tw - 1), f(th * ty), f(th * ty + th - 1)
     if X0 <= mx <= X1 and Y0 <= my <= Y1:
         return bool(f(0) <= pr["qlim"][g])
     best = None
@@ -325,10 +326,11 @@ def _keep_scalar(pr, g, tx, ty):
     return bool(best <= pr["qlim"][g])
 
 
-def test_binning_matches_brute_force_rect_enumeration():
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8), (64, 4)])
+def test_binning_matches_brute_force_rect_enumeration(tile):
     sc, cams = scenes.small_room(n=600, n_cams=2, seed=9)
-    b1 = ob.bin_cameras(sc, cams)
-    b2 = ob.bin_cameras_fast(sc, cams)
+    b1 = ob.bin_cameras(sc, cams, tile)
+    b2 = ob.bin_cameras_fast(sc, cams, tile)
     assert np.array_equal(b1["keys"], b2["keys"]) and np.array_equal(b1["vals"], b2["vals"])
     assert np.array_equal(b1["ranges"], b2["ranges"])
     # brute force: per tile, every Gaussian whose rectangle contains it and that
@@ -337,17 +339,47 @@ def test_binning_matches_brute_force_rect_enumeration():
     for k, cam in enumerate(cams):
         pr = b1["projs"][k]
         TX, TY = pr["tiles_x"], pr["tiles_y"]
+        assert (TX, TY) == (-(-cam.width // tile[0]), -(-cam.height // tile[1]))
         x0, x1, y0, y1 = pr["rect"]
+        # the rectangle covers the 3-sigma square [m - r, m + r] of every
+        # valid Gaussian, in tiles of the requested shape
+        v = pr["valid"]
+        m, r = pr["mean2d"], pr["radius"]
+        lo_x = np.clip(np.floor((m[0] - r) / tile[0]), 0, TX)
+        hi_x = np.clip(np.ceil((m[0] + r) / tile[0]), 0, TX)
+        assert np.array_equal(x0[v], lo_x[v]) and np.array_equal(x1[v], hi_x[v])
+        lo_y = np.clip(np.floor((m[1] - r) / tile[1]), 0, TY)
+        hi_y = np.clip(np.ceil((m[1] + r) / tile[1]), 0, TY)
+        assert np.array_equal(y0[v], lo_y[v]) and np.array_equal(y1[v], hi_y[v])
         for t in range(TX * TY):
             ty, tx = divmod(t, TX)
             inside = pr["valid"] & (x0 <= tx) & (tx < x1) & (y0 <= ty) & (ty < y1)
-            ids = [g for g in np.nonzero(inside)[0] if _keep_scalar(pr, g, tx, ty)]
+            ids = [g for g in np.nonzero(inside)[0] if _keep_scalar(pr, g, tx, ty, tile)]
             n_culled += int(inside.sum()) - len(ids)
             ids = np.array(ids, dtype=np.int64)
             ids = ids[np.lexsort((ids, pr["zbits"][ids]))] if ids.size else ids
             s0, s1 = b1["ranges"][b1["tile_offset"][k] + t]
             assert np.array_equal(b1["vals"][s0:s1], ids)
     assert n_culled > 0
+
+
+def test_render_does_not_depend_on_tile_shape():
+    """The tile shape decides which (tile, Gaussian) pairs are listed, but the
+    opacity-aware test drops only pairs whose alpha stays below 1/255 on the
+    whole tile, and every tile's list is ordered by (depth, index): each pixel
+    blends the same Gaussians in the same order for every shape."""
+    sc, cams = scenes.small_room(n=3000, width=70, height=52, n_sem=4, seed=19, n_cams=2)
+    ref = None
+    for tile in ((16, 16), (8, 32), (32, 8), (64, 4)):
+        _, outs, b = oracle.render(sc, cams, with_normal_d=False, tile=tile)
+        assert b["tile"] == tile
+        if ref is None:
+            ref = outs
+            continue
+        for o, o0 in zip(outs, ref):
+            for key in ("rgb", "depth", "normal", "kmap", "logits", "T"):
+                assert torch.allclose(o[key], o0[key], rtol=1e-12, atol=1e-13), (tile, key)
+            assert torch.equal(o["n_used"], o0["n_used"])
 
 
 def test_tile_culling_is_conservative():
@@ -379,12 +411,13 @@ def test_tile_culling_is_conservative():
 
 # -------------------------------------------------------- compositing
 def _brute_force_pixel(prep, binproj, cam, u, v, ids_all):
-    """Alg. 2 for one pixel, sequentially, over every Gaussian whose tile
-    rectangle contains the pixel's tile, ordered by (depth bits, index)."""
-    tx, ty = u // 16, v // 16
-    x0, x1, y0, y1 = binproj["rect"]
-    sel = [g for g in ids_all if binproj["valid"][g] and x0[g] <= tx < x1[g]
-           and y0[g] <= ty < y1[g]]
+    """Alg. 2 for one pixel, sequentially, over every Gaussian the recipe keeps
+    whose 3-sigma square |u - m_x| <= r, |v - m_y| <= r contains the pixel -
+    no tiles involved - ordered by (depth bits, index)."""
+    m64 = prep.mean2d.numpy()
+    r = binproj["radius"]
+    sel = [g for g in ids_all if binproj["valid"][g] and abs(u - m64[g, 0]) <= r[g]
+           and abs(v - m64[g, 1]) <= r[g]]
     sel.sort(key=lambda g: (int(binproj["zbits"][g]), g))
     d, zc = orr.pixel_rays(cam, torch.tensor([[float(u), float(v)]], dtype=F64))
     T = 1.0
