@@ -154,8 +154,18 @@ def launch_shape(cfg, simt_logits: bool) -> dict:
         fwd = (int(cfg.batch_fwd) or 32, int(cfg.ctas_per_sm_fwd) or 2)
     else:
         fwd = (int(cfg.batch_fwd) or 16, min(int(cfg.ctas_per_sm_fwd) or 4, 4))
-    return {"fwd": {"batch": fwd[0], "ctas_per_sm": fwd[1]},
+    return {"tile": [int(cfg.tile_w) or 16, int(cfg.tile_h) or 16],
+            "fwd": {"batch": fwd[0], "ctas_per_sm": fwd[1]},
             "bwd": {"batch": bwd[0], "ctas_per_sm": bwd[1]}}
+
+
+def parse_tile(text: str) -> tuple:
+    """'WxH' -> (W, H); one of the library's 256-pixel tile shapes."""
+    from paper_2510_12174_gb300 import abi
+    w, h = (int(v) for v in text.lower().split("x"))
+    if (w, h) not in abi.TILE_SHAPES:
+        raise SystemExit(f"--tile {text}: not one of {abi.TILE_SHAPES}")
+    return w, h
 
 
 def aggregate(ms_local: float, world: int, device) -> tuple:
@@ -434,6 +444,7 @@ def run_ours(args):
     cfg = abi.unigs_config_default()
     cfg.batch, cfg.ctas_per_sm = args.batch, args.ctas
     cfg.batch_fwd, cfg.ctas_per_sm_fwd = args.batch_fwd, args.ctas_fwd
+    cfg.tile_w, cfg.tile_h = parse_tile(args.tile)
     if args.simt_logits:
         cfg.flags |= abi.UNIGS_FLAG_SIMT_LOGITS
     r = rz.Renderer(ds, cams, cfg=cfg)
@@ -966,6 +977,9 @@ def main():
                     help="forward composite batch (0: library default)")
     ap.add_argument("--ctas-fwd", type=int, default=0,
                     help="forward composite CTAs per SM (0: library default)")
+    ap.add_argument("--tile", default="16x16",
+                    help="tile shape WxH of the binning and the composites "
+                         "(16x16, 8x32, 32x8 or 64x4)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

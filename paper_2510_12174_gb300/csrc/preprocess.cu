@@ -37,9 +37,11 @@ struct Recipe {
 
 __device__ __forceinline__ void rect_axis(float m, float r, int n_tiles, int side, int* lo,
                                           int* hi) {
-    const float nt = (float)n_tiles;
-    float l = floorf(__fdiv_rn(RS(m, r), (float)side));
-    float h = ceilf(__fdiv_rn(RA(m, r), (float)side));
+    // side is a power of two, so multiplying by its exact reciprocal gives
+    // the bits of the division
+    const float nt = (float)n_tiles, inv = 1.f / (float)side;
+    float l = floorf(__fmul_rn(RS(m, r), inv));
+    float h = ceilf(__fmul_rn(RA(m, r), inv));
     l = fminf(fmaxf(l, 0.f), nt);
     h = fminf(fmaxf(h, 0.f), nt);
     *lo = (int)l;
@@ -401,10 +403,12 @@ __global__ void __launch_bounds__(256)
         }
         {
             // box of the q <= qlim ellipse (x half-extent sqrt(qlim * Sigma_xx)),
-            // with a relative and a one-pixel margin
+            // with a relative and a one-pixel margin, clipped to the 3-sigma
+            // square (plus a margin far above the float32 error of the centre)
             const float ql = fmaxf(cr[C_QLIM], 0.f);
-            o[R_EXTX] = sqrtf(ql * sf.cxx) * 1.01f + 1.f;
-            o[R_EXTY] = sqrtf(ql * sf.cyy) * 1.01f + 1.f;
+            const float sq = rc.radius + 0.01f;
+            o[R_EXTX] = fminf(sqrtf(ql * sf.cxx) * 1.01f + 1.f, sq);
+            o[R_EXTY] = fminf(sqrtf(ql * sf.cyy) * 1.01f + 1.f, sq);
         }
         float4* dst = reinterpret_cast<float4*>(rec + (size_t)t * REC_FLOATS);
 #pragma unroll

@@ -23,15 +23,13 @@ __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float
     const float vy = __fsub_rn(vf, rc[R_MYH]);
     const float r3 = rc[R_R3];
     float q;
+    bool outside;
     if (rc[R_FLAG] != 0.f) {
         const ff dx = two_sum(ux, -rc[R_MXL]);
         const ff dy = two_sum(vy, -rc[R_MYL]);
         *dx_out = ff_val(dx);
         *dy_out = ff_val(dy);
-        if (fabsf(*dx_out) > r3 || fabsf(*dy_out) > r3) {
-            *gauss_out = 0.f;
-            return -1.f;
-        }
+        outside = fmaxf(fabsf(*dx_out), fabsf(*dy_out)) > r3;
         const ff A = {rc[R_CON], rc[R_CLO]}, B = {rc[R_CON + 1], rc[R_CLO + 1]},
                  C = {rc[R_CON + 2], rc[R_CLO + 2]};
         const ff t1 = ff_mul(A, ff_mul(dx, dx));
@@ -43,17 +41,16 @@ __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float
         const float dy = __fsub_rn(vy, rc[R_MYL]);
         *dx_out = dx;
         *dy_out = dy;
-        if (fabsf(dx) > r3 || fabsf(dy) > r3) {
-            *gauss_out = 0.f;
-            return -1.f;
-        }
+        outside = fmaxf(fabsf(dx), fabsf(dy)) > r3;
         const float A = rc[R_CON], B = rc[R_CON + 1], C = rc[R_CON + 2];
         q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(C, dy), dy)),
                       __fmul_rn(2.f, __fmul_rn(__fmul_rn(B, dx), dy)));
     }
+    // the square test is applied as a select, after the exponential, so the
+    // warp does not diverge ahead of it
     const float G = __expf(__fmul_rn(-0.5f, q));
-    *gauss_out = G;
-    return fminf(alpha_max, __fmul_rn(rc[R_OP], G));
+    *gauss_out = outside ? 0.f : G;
+    return outside ? -1.f : fminf(alpha_max, __fmul_rn(rc[R_OP], G));
 }
 
 // u = K D (conic times pixel offset), the direction of every alpha gradient:
