@@ -309,6 +309,19 @@ unigs_status unigs_stats_poll(const unigs_plan* plan, const void* ws, int64_t* p
  * plan (the count is fixed by the plan). */
 int32_t unigs_launches_per_step(const unigs_plan* plan);
 
+/* The composite kernels this plan runs, fixed at plan time by the logit width,
+ * the feature dtype, UNIGS_FLAG_SIMT_LOGITS and the launch shapes: a bit set
+ * of UNIGS_PATH_*.  UNIGS_PATH_FWD_TC: the forward blends the logits on the
+ * tensor cores (9..64 logits).  UNIGS_PATH_BWD_TC: the backward forms the
+ * logit terms of Alg. 4 on the tensor cores (bfloat16 logits, 9..64 of them,
+ * backward shape default or batch 16 x 2 CTAs per SM).  UNIGS_PATH_SEM32:
+ * unigs_preprocess makes a float32 copy of bfloat16 logit rows for an
+ * FP32-pipe composite.  0 for a NULL plan. */
+#define UNIGS_PATH_FWD_TC 1
+#define UNIGS_PATH_BWD_TC 2
+#define UNIGS_PATH_SEM32 4
+int32_t unigs_plan_paths(const unigs_plan* plan);
+
 const char* unigs_status_string(unigs_status s);
 
 /* Allocation-free sort (the paper has no counterpart: this is a service for

@@ -22,6 +22,9 @@ UNIGS_MAX_SEM = 64
 UNIGS_FLAG_CENTER_DEPTH = 1
 UNIGS_FLAG_SIMT_LOGITS = 2
 UNIGS_FLAG_CHECK_FINITE = 4
+UNIGS_PATH_FWD_TC = 1
+UNIGS_PATH_BWD_TC = 2
+UNIGS_PATH_SEM32 = 4
 UNIGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 
 UNIGS_OK = 0
@@ -145,6 +148,7 @@ _SIGS = [
     ("unigs_stats_poll", c_int32, [POINTER(unigs_plan), c_void_p, POINTER(c_int64),
                                    POINTER(c_int64), c_void_p]),
     ("unigs_launches_per_step", c_int32, [POINTER(unigs_plan)]),
+    ("unigs_plan_paths", c_int32, [POINTER(unigs_plan)]),
     ("unigs_status_string", c_char_p, [c_int32]),
     ("unigs_sort_pairs_static", c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                           c_void_p, c_void_p]),
@@ -275,6 +279,10 @@ def unigs_probe_fma(sink, iters, packed, flops_out, stream) -> int:
 
 def unigs_launches_per_step(plan) -> int:
     return lib().unigs_launches_per_step(ctypes.byref(plan))
+
+
+def unigs_plan_paths(plan) -> int:
+    return lib().unigs_plan_paths(ctypes.byref(plan))
 
 
 # include/unigs_train.h ---------------------------------------------------------

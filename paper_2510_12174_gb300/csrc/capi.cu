@@ -218,7 +218,8 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     sizes[OFF_GREC] = sizeof(double) * GREC_FLOATS * (size_t)total;
     sizes[OFF_CULL] = sizeof(float) * CULL_FLOATS * (size_t)total;
     // float32 copy of bfloat16 semantic rows, refreshed by every preprocess
-    sizes[OFF_SEM32] = g->feat_dtype ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
+    // when an FP32-pipe composite will read it
+    sizes[OFF_SEM32] = sem32_needed(*plan) ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
     sizes[OFF_ORDER] = sizeof(uint32_t) * (size_t)tiles;
     sizes[OFF_LOSS] = sizeof(float) * 8 * (size_t)LOSS_MAX_BLOCKS;
     size_t off = 0;
@@ -342,13 +343,24 @@ int32_t unigs_launches_per_step(const unigs_plan* plan) {
     const int per_pass = 1 + 3 + 1;
     const int bin = 3 + 1 + per_pass * plan->sort_passes + 1 + 1 /*tile order*/;
     int conv = 0;
-    if (plan->feat_dtype && plan->n_sem > 0 && plan->n > 0) {
+    if (sem32_needed(*plan)) {
         const int64_t cnt = plan->n * (int64_t)plan->n_sem;
         conv = (cnt / 2 > 0 ? 1 : 0) + (int)(cnt & 1);
     }
     const int check = (plan->cfg.flags & UNIGS_FLAG_CHECK_FINITE) && plan->n > 0 ? 1 : 0;
     return 2 /*preprocess*/ + check + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ +
            2 /*bwd*/;
+}
+
+int32_t unigs_plan_paths(const unigs_plan* plan) {
+    if (!plan) return 0;
+    int32_t bits = 0;
+    if (plan->n_sem >= 9 && plan->n_sem <= UNIGS_MAX_SEM &&
+        !(plan->cfg.flags & UNIGS_FLAG_SIMT_LOGITS))
+        bits |= UNIGS_PATH_FWD_TC;
+    if (bwd_tc_selected(*plan)) bits |= UNIGS_PATH_BWD_TC;
+    if (sem32_needed(*plan)) bits |= UNIGS_PATH_SEM32;
+    return bits;
 }
 
 // ------------------------------------------------------------ training step

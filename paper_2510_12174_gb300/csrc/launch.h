@@ -14,6 +14,15 @@ int launch_render_fwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_outputs& out, cudaStream_t st);
 // Tensor-core logit blend variant of the forward (bfloat16 logits, 9..64).
 bool fwd_tc_eligible(const unigs_plan& p, const unigs_gaussians& g);
+// Backward composite on the tensor cores: bfloat16 logits (9..64 channels),
+// no UNIGS_FLAG_SIMT_LOGITS, launch shape default or batch 16 x 2 CTAs/SM.
+bool bwd_tc_selected(const unigs_plan& p);
+int launch_render_bwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws,
+                         const unigs_outputs& fwd, const unigs_grad_outputs& go,
+                         const unigs_param_grads& grads, double* grec, cudaStream_t st);
+// Whether a float32 copy of bfloat16 logit rows is made per step: only the
+// FP32-pipe composites read it.
+bool sem32_needed(const unigs_plan& p);
 int launch_render_fwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                          const unigs_outputs& out, cudaStream_t st);
 int launch_depth_normal_fwd(const unigs_plan& p, const CamTable& tab, const float* depth,

@@ -14,6 +14,7 @@
 // the camera-frame pixel ray d~ = ((u-cx)/fx, (v-cy)/fy, 1) to the local
 // scaled direction, d_s = S^-1 R^T R_cw d~ = M_c d~; plus N_w = R S^-1, which
 // maps a scaled-local surface point to the world-frame ellipsoid normal.
+#include "ewa_ff.cuh"
 #include "launch.h"
 #include "ff.cuh"
 #include "sh.cuh"
@@ -139,6 +140,7 @@ struct SplatFF {
     ff A, B, C;
     float kappa;
     float cxx, cyy;  // diagonal of the 2D covariance
+    float ec, es;    // principal axis e0 = (ec, es) of the 2D covariance
 };
 
 __device__ __forceinline__ void split_center(ff m, float* hi, float* lo) {
@@ -150,53 +152,10 @@ __device__ __forceinline__ void split_center(ff m, float* hi, float* lo) {
 __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy, float muz,
                                          float qw, float qx, float qy, float qz, float sx,
                                          float sy, float sz, float lowpass, SplatFF& o) {
-    const float* W = cam.R_wc;
-    ff pc[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-        pc[i] = ff_add(ff_add(ff_add(two_prod(W[3 * i], mux), two_prod(W[3 * i + 1], muy)),
-                              two_prod(W[3 * i + 2], muz)),
-                       ff_from(cam.t_wc[i]));
-    const ff n2 = ff_add(ff_add(two_prod(qw, qw), two_prod(qx, qx)),
-                         ff_add(two_prod(qy, qy), two_prod(qz, qz)));
-    const ff qn = ff_sqrt(n2);
-    const ff w = ff_div(ff_from(qw), qn), x = ff_div(ff_from(qx), qn),
-             y = ff_div(ff_from(qy), qn), z = ff_div(ff_from(qz), qn);
-    const ff one = ff_from(1.f);
-    ff R[3][3];
-    R[0][0] = ff_sub(one, ff_scale(ff_add(ff_mul(y, y), ff_mul(z, z)), 2.f));
-    R[0][1] = ff_scale(ff_sub(ff_mul(x, y), ff_mul(w, z)), 2.f);
-    R[0][2] = ff_scale(ff_add(ff_mul(x, z), ff_mul(w, y)), 2.f);
-    R[1][0] = ff_scale(ff_add(ff_mul(x, y), ff_mul(w, z)), 2.f);
-    R[1][1] = ff_sub(one, ff_scale(ff_add(ff_mul(x, x), ff_mul(z, z)), 2.f));
-    R[1][2] = ff_scale(ff_sub(ff_mul(y, z), ff_mul(w, x)), 2.f);
-    R[2][0] = ff_scale(ff_sub(ff_mul(x, z), ff_mul(w, y)), 2.f);
-    R[2][1] = ff_scale(ff_add(ff_mul(y, z), ff_mul(w, x)), 2.f);
-    R[2][2] = ff_sub(one, ff_scale(ff_add(ff_mul(x, x), ff_mul(y, y)), 2.f));
-    const float s[3] = {sx, sy, sz};
-    ff M[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) M[i][j] = ff_mul_f(R[i][j], s[j]);
-    const ff iz = ff_div(one, pc[2]);
-    const ff xz = ff_mul(pc[0], iz), yz = ff_mul(pc[1], iz);
-    const ff J00 = ff_mul_f(iz, cam.fx), J11 = ff_mul_f(iz, cam.fy);
-    const ff J02 = ff_neg(ff_mul(J00, xz)), J12 = ff_neg(ff_mul(J11, yz));
-    // V = T M with T = J R_wc (2x3); cov = V V^T + lowpass I
-    ff T[2][3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        T[0][j] = ff_add(ff_mul_f(J00, W[j]), ff_mul_f(J02, W[6 + j]));
-        T[1][j] = ff_add(ff_mul_f(J11, W[3 + j]), ff_mul_f(J12, W[6 + j]));
-    }
-    ff V[2][3];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            V[i][j] = ff_add(ff_add(ff_mul(T[i][0], M[0][j]), ff_mul(T[i][1], M[1][j])),
-                             ff_mul(T[i][2], M[2][j]));
+    EwaFF e;
+    ewa_ff(cam, mux, muy, muz, qw, qx, qy, qz, sx, sy, sz, e);
+    const ff(&V)[2][3] = e.V;
+    const ff xz = e.xz, yz = e.yz;
     const ff lp = ff_from(lowpass);
     const ff c00 = ff_add(ff_add(ff_add(ff_mul(V[0][0], V[0][0]), ff_mul(V[0][1], V[0][1])),
                                  ff_mul(V[0][2], V[0][2])), lp);
@@ -207,6 +166,10 @@ __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy
     const ff det = ff_sub(ff_mul(c00, c11), ff_mul(c01, c01));
     o.cxx = ff_val(c00);
     o.cyy = ff_val(c11);
+    // principal axes: e0 at theta = atan2(2 c01, c00 - c11) / 2 (any
+    // orthonormal pair is a valid frame; this one keeps the recorded
+    // covariance gradient free of cancellation for thin splats)
+    sincosf(0.5f * atan2f(2.f * ff_val(c01), ff_val(ff_sub(c00, c11))), &o.es, &o.ec);
     o.A = ff_div(c11, det);
     o.B = ff_neg(ff_div(c01, det));
     o.C = ff_div(c00, det);
@@ -337,6 +300,9 @@ __global__ void __launch_bounds__(256)
         o[R_CLO + 1] = sf.B.lo;
         o[R_CLO + 2] = sf.C.lo;
         o[R_FLAG] = sf.kappa > KAPPA_FF ? 1.f : 0.f;
+        o[R_EC] = sf.ec;
+        o[R_ES] = sf.es;
+        o[R_ES + 1] = o[R_ES + 2] = 0.f;
 
         // colour from SH, viewing direction mu - C
         float dx = mux - cam.C[0], dy = muy - cam.C[1], dz = muz - cam.C[2];
@@ -505,7 +471,7 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
             ws_ptr<float>(ws, p, OFF_CULL));
         ++launches;
     }
-    if (p.feat_dtype && p.n_sem > 0 && p.n > 0) {
+    if (sem32_needed(p)) {
         // n * n_sem is even whenever n_sem is (rows of 2-element pairs); an odd
         // count leaves the last element to a one-element tail launch
         const int64_t cnt = p.n * (int64_t)p.n_sem;

@@ -28,7 +28,8 @@
 
 #include "launch.h"
 #include "sh.cuh"
-#include "splat.cuh"
+#include "bwd_pair.cuh"
+#include "ewa_ff.cuh"
 
 namespace unigs {
 
@@ -151,12 +152,6 @@ __device__ __forceinline__ void bwd_issue(const BwdParams& P, BwdSmem<NS, B>& S,
     if (lane == 0) mbar_arrive(&S.bar[buf]);
 }
 
-__device__ __forceinline__ void cross_acc(const float* a, const float* b, float* c) {
-    c[0] += a[1] * b[2] - a[2] * b[1];
-    c[1] += a[2] * b[0] - a[0] * b[2];
-    c[2] += a[0] * b[1] - a[1] * b[0];
-}
-
 template <int NS, int B>
 // batch 8 (73 KB of shared memory at 64 logits): 3 CTAs per SM, 80 registers;
 // larger batches (80 KB at 16, 94 KB at 32): 2 CTAs per SM, 128 registers
@@ -222,7 +217,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
 
         float T = 1.f;
         uint32_t last = 0;
-        float g_rgb[3] = {0.f, 0.f, 0.f}, g_D = 0.f, g_N[3] = {0.f, 0.f, 0.f}, g_K = 0.f;
+        PixelUp up = {{0.f, 0.f, 0.f}, 0.f, {0.f, 0.f, 0.f}, 0.f};
         // upstream logit gradients of this pixel -> shared memory row tid (zero
         // padded), read by this thread for G_i and by the warp's channel gather
 #pragma unroll 8
@@ -232,14 +227,7 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
         if (inside) {
             T = P.T_final[pix + idx];
             last = P.n_contrib[pix + idx];
-            if (P.go.rgb)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) g_rgb[c] = P.go.rgb[pix * 3 + c * HW + idx];
-            if (P.go.depth) g_D = P.go.depth[pix + idx];
-            if (P.go.normal_g)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) g_N[c] = P.go.normal_g[pix * 3 + c * HW + idx];
-            if (P.go.kmap) g_K = P.go.kmap[pix + idx];
+            load_pixel_up(P.go, pix, HW, idx, up);
         }
         if (last) atomicMax(&S.max_last, last);
         // the warp's own last list position: Gaussians behind it are skipped
@@ -293,118 +281,9 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 const bool contrib = !timed_out && pos < last && alpha >= P.alpha_min;
                 if (!__any_sync(0xffffffffu, contrib)) continue;
                 float gv[32];
-                const float om = 1.f - alpha;
-                // om >= 1 - alpha_max.  The restoration T <- T / om runs along
-                // the whole list, so it keeps the correctly rounded division
-                // (with an approximate quotient the worst cancelling rotation
-                // gradient of a 200k-Gaussian test scene drifted 2.5x further
-                // from the float64 reference); dL/dalpha takes an approximate
-                // reciprocal
-                const float rom = __fdividef(1.f, om);
-                if (contrib) T = __fdiv_rn(T, om);
-                const float w = contrib ? alpha * T : 0.f;
-                PairGeom G;
-                pair_geometry(rc, xt, yt, dx, dy, G);
-                const float depth = P.center_depth ? rc[R_Z] : G.t;
-                const float sg = G.inside ? -1.f : 1.f;
-                float nh[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) nh[i] = G.m[i] * G.inv_m;
-                // G_i: upstream gradient . features of Gaussian i
-                const float Gi = g_rgb[0] * rc[R_RGB] + g_rgb[1] * rc[R_RGB + 1] +
-                                 g_rgb[2] * rc[R_RGB + 2] + g_D * depth + g_K * rc[R_K] +
-                                 sg * (g_N[0] * nh[0] + g_N[1] * nh[1] + g_N[2] * nh[2]) +
-                                 sem_dot<NS>(a_row, &S.sem[buf][j][0]);
-                const float dL_da = contrib ? T * Gi - Sacc * rom : 0.f;
-                Sacc = fmaf(w, Gi, Sacc);
-                // alpha = min(alpha_max, op * Gs)
-                const bool clamped = rc[R_OP] * Gs > P.alpha_max;
-                const float g_pow = clamped ? 0.f : dL_da * alpha;
-                gv[G_OP] = clamped ? 0.f : dL_da * Gs;
-                // power = -1/2 D^T K D: dL/dm = g u, dL/dcov = g/2 u u^T, u = K D
-                float kux, kuy;
-                splat_kdelta(rc, uf, vf, dx, dy, &kux, &kuy);
-                gv[G_CA] = 0.5f * g_pow * kux * kux;
-                gv[G_CB] = g_pow * kux * kuy;
-                gv[G_CC] = 0.5f * g_pow * kuy * kuy;
-                gv[G_MX] = kux * g_pow;
-                gv[G_MY] = kuy * g_pow;
-                gv[G_RGB] = w * g_rgb[0];
-                gv[G_RGB + 1] = w * g_rgb[1];
-                gv[G_RGB + 2] = w * g_rgb[2];
-                gv[G_K] = w * g_K;
-                const float* Nw = rc + R_NW;
-                const float inv_a = __fdividef(1.f, G.a);
-                // The Gaussian enters through v_s and d_s.  Besides g_vs the
-                // record takes B = g_vs (x) w + G2 (x) d_s with w = v_s + t d_s
-                // (the closest-approach point p_mid, formed without
-                // cancellation) and G2 = g_ds - t g_vs, which is small and is
-                // formed here term by term: g_vs (x) v_s and g_ds (x) d_s are
-                // both large for a Gaussian far from the camera and would cancel
-                // in the scale and rotation gradients (B equals their sum).
-                // g_a collects the normal's dependence on a = d_s.d_s only.
-                float g_vs[3] = {0.f, 0.f, 0.f}, g2[3] = {0.f, 0.f, 0.f}, g_a = 0.f;
-                // depth t_mid = -b'/a: g_vs = g_bp d_s, g_ds = g_bp (v_s + 2 t d_s),
-                // so its part of G2 is g_bp w
-                const float g_t = w * g_D;
-                gv[G_Z] = P.center_depth ? g_t : 0.f;
-                if (!P.center_depth) {
-                    const float g_bp = -g_t * inv_a;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        g_vs[i] = g_bp * G.ds[i];
-                        g2[i] = g_bp * G.pm[i];
-                    }
-                }
-                // normal n = sg * m / |m|, m = N_w p
-                const float gn[3] = {w * g_N[0], w * g_N[1], w * g_N[2]};
-                const float dgn = gn[0] * nh[0] + gn[1] * nh[1] + gn[2] * nh[2];
-                float g_m[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) g_m[i] = sg * (gn[i] - dgn * nh[i]) * G.inv_m;
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) gv[G_NW + 3 * r + c] = g_m[r] * G.p[c];
-                float g_p[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    g_p[c] = Nw[c] * g_m[0] + Nw[3 + c] * g_m[1] + Nw[6 + c] * g_m[2];
-                // p = p_mid - sr h d_s, h = sqrt(disc)/a
-                float g_disc = 0.f;
-                if (G.hit) {
-                    const float g_h = -G.sr * (g_p[0] * G.ds[0] + g_p[1] * G.ds[1] +
-                                               g_p[2] * G.ds[2]);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) g2[i] -= G.sr * G.h * g_p[i];
-                    // dh/ddisc = 1 / (2 a sqrt(disc))
-                    g_disc = 0.5f * g_h * inv_a * rsqrtf(G.disc);
-                    g_a -= g_h * G.h * inv_a;
-                }
-                // disc = a - |cv|^2
-                g_a += g_disc;
-                float g_cv[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) g_cv[i] = -2.f * g_disc * G.cv[i];
-                // p_mid = (d_s x cv) / a
-                const float g_q[3] = {g_p[0] * inv_a, g_p[1] * inv_a, g_p[2] * inv_a};
-                cross_acc(G.cv, g_q, g2);
-                cross_acc(g_q, G.ds, g_cv);
-                g_a -= (g_p[0] * G.pm[0] + g_p[1] * G.pm[1] + g_p[2] * G.pm[2]) * inv_a;
-                // cv = v_s x d_s: g_vs += d_s x g_cv, and g_ds += g_cv x v_s,
-                // whose part of G2 is g_cv x v_s - t (d_s x g_cv) = g_cv x w
-                cross_acc(G.ds, g_cv, g_vs);
-                cross_acc(g_cv, G.pm, g2);
-                // a = d_s . d_s
-#pragma unroll
-                for (int i = 0; i < 3; ++i) g2[i] = fmaf(2.f * g_a, G.ds[i], g2[i]);
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        gv[G_B + 3 * r + c] = fmaf(g_vs[r], G.pm[c], g2[r] * G.ds[c]);
-                    gv[G_VS + r] = g_vs[r];
-                }
+                const float w = bwd_pair(rc, up, xt, yt, uf, vf, dx, dy, alpha, Gs, contrib,
+                                         sem_dot<NS>(a_row, &S.sem[buf][j][0]), P.alpha_max,
+                                         P.center_depth, T, Sacc, gv);
                 {
                     const uint32_t g = S.ids[buf][j];
                     const size_t rix = (size_t)cam_idx * (size_t)P.n + g;
@@ -520,12 +399,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
         R[2][1] = 2.f * (y * z + w * x);
         R[2][2] = 1.f - 2.f * (x * x + y * y);
         const float is[3] = {1.f / s[0], 1.f / s[1], 1.f / s[2]};
-        float M[3][3], Sig[3][3];
+        float M[3][3];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) M[a][b] = R[a][b] * s[b];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b)
-                Sig[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
 
         float g_mu[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {}, g_s[3] = {0.f, 0.f, 0.f};
         float g_th[3] = {0.f, 0.f, 0.f};  // rotation R -> R exp([theta]_x)
@@ -593,23 +469,60 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
                 Tm[0][j] = J00 * Wr[j] + J02 * Wr[6 + j];
                 Tm[1][j] = J11 * Wr[3 + j] + J12 * Wr[6 + j];
             }
-            float U[2][3];
+            // The record holds G' = dL/d(2D covariance) in the splat's
+            // principal frame E (columns e0 = (ec, es), e1 = (-es, ec)), so
+            // G = E G' E^T.  With V' = E^T T M (M = R S: the projected scaled
+            // axes in that frame) every product below stays free of
+            // cancellation, also for a thin splat seen far off-axis, where
+            // T^T G T has entries orders of magnitude above the gradients.
+            const float* rp = P.rec + t * REC_FLOATS;
+            const float ec = rp[R_EC], es = rp[R_ES];
+            float Vp[2][3];
+            if (rp[R_FLAG] != 0.f) {
+                // ill-conditioned splat: V' in double-float (its short-axis
+                // row is orders of magnitude below T M's entries)
+                EwaFF e;
+                ewa_ff(cam, mu[0], mu[1], mu[2], q0[0], q0[1], q0[2], q0[3], s[0], s[1], s[2], e);
+                for (int j = 0; j < 3; ++j) {
+                    Vp[0][j] = ff_val(ff_add(ff_mul_f(e.V[0][j], ec), ff_mul_f(e.V[1][j], es)));
+                    Vp[1][j] = ff_val(ff_add(ff_mul_f(e.V[0][j], -es), ff_mul_f(e.V[1][j], ec)));
+                }
+            } else {
+                for (int j = 0; j < 3; ++j) {
+                    float tm[2];
+                    for (int a = 0; a < 2; ++a)
+                        tm[a] = Tm[a][0] * M[0][j] + Tm[a][1] * M[1][j] + Tm[a][2] * M[2][j];
+                    Vp[0][j] = ec * tm[0] + es * tm[1];
+                    Vp[1][j] = -es * tm[0] + ec * tm[1];
+                }
+            }
+            const float Gp[2][2] = {{gr[G_CA], 0.5f * gr[G_CB]}, {0.5f * gr[G_CB], gr[G_CC]}};
+            float GV[2][3];
             for (int a = 0; a < 2; ++a)
-                for (int j = 0; j < 3; ++j)
-                    U[a][j] = Tm[a][0] * Sig[0][j] + Tm[a][1] * Sig[1][j] + Tm[a][2] * Sig[2][j];
-            // the record holds dL/d(a, b, c) of the 2D covariance [[a, b], [b, c]]
-            const float Gc[2][2] = {{gr[G_CA], 0.5f * gr[G_CB]}, {0.5f * gr[G_CB], gr[G_CC]}};
-            // dL/dSigma = T^T G T
-            float gSig[3][3];
+                for (int j = 0; j < 3; ++j) GV[a][j] = Gp[a][0] * Vp[0][j] + Gp[a][1] * Vp[1][j];
+            // H = V'^T G' V' = S (T R)^T G (T R) S.  Sigma = R S^2 R^T:
+            // dL/ds_b = 2 H_bb / s_b, and for R -> R exp([theta]_x)
+            // dL/dtheta_k = 2 (s_i / s_j - s_j / s_i) H_ij, (i, j, k) cyclic
+            float H[3][3];
             for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b)
-                    gSig[a][b] = Tm[0][a] * (Gc[0][0] * Tm[0][b] + Gc[0][1] * Tm[1][b]) +
-                                 Tm[1][a] * (Gc[1][0] * Tm[0][b] + Gc[1][1] * Tm[1][b]);
-            // dL/dT = 2 G T Sigma
+                for (int b = 0; b < 3; ++b) H[a][b] = Vp[0][a] * GV[0][b] + Vp[1][a] * GV[1][b];
+            for (int b = 0; b < 3; ++b) g_s[b] += 2.f * H[b][b] * is[b];
+            g_th[0] += 2.f * (s[1] * is[2] - s[2] * is[1]) * H[1][2];
+            g_th[1] += 2.f * (s[2] * is[0] - s[0] * is[2]) * H[2][0];
+            g_th[2] += 2.f * (s[0] * is[1] - s[1] * is[0]) * H[0][1];
+            // dL/dT = 2 G T Sigma = 2 E (G' V') M^T
             float gT[2][3];
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 3; ++b)
-                    gT[a][b] = 2.f * (Gc[a][0] * U[0][b] + Gc[a][1] * U[1][b]);
+            {
+                float EGV[2][3];
+                for (int j = 0; j < 3; ++j) {
+                    EGV[0][j] = ec * GV[0][j] - es * GV[1][j];
+                    EGV[1][j] = es * GV[0][j] + ec * GV[1][j];
+                }
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        gT[a][b] = 2.f * (EGV[a][0] * M[b][0] + EGV[a][1] * M[b][1] +
+                                          EGV[a][2] * M[b][2]);
+            }
             const float gJ00 = gT[0][0] * Wr[0] + gT[0][1] * Wr[1] + gT[0][2] * Wr[2];
             const float gJ02 = gT[0][0] * Wr[6] + gT[0][1] * Wr[7] + gT[0][2] * Wr[8];
             const float gJ11 = gT[1][0] * Wr[3] + gT[1][1] * Wr[4] + gT[1][2] * Wr[5];
@@ -623,14 +536,6 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
                       gr[G_Z];
             for (int a = 0; a < 3; ++a)
                 g_mu[a] += Wr[a] * g_pc[0] + Wr[3 + a] * g_pc[1] + Wr[6 + a] * g_pc[2];
-            // Sigma = M M^T, M = R S: dL/dM = 2 gSig M (gSig symmetric)
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    const float gM = 2.f * (gSig[a][0] * M[0][b] + gSig[a][1] * M[1][b] +
-                                            gSig[a][2] * M[2][b]);
-                    g_R[a][b] += gM * s[b];
-                    g_s[b] += gM * R[a][b];
-                }
 
             // ---- ray-ellipsoid setup (Sec. 3.2): v_s = S^-1 R^T (C - mu) and
             // d_s = S^-1 R^T d.  The record holds g_vs and B (= g_vs (x) v_s +
@@ -729,7 +634,9 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
     cudaMemsetAsync(grec, 0, sizeof(double) * GREC_FLOATS * (size_t)p.n * p.n_cams, st);
     if (grads.sem && !grads.accumulate && p.n_sem > 0)
         cudaMemsetAsync(grads.sem, 0, sizeof(float) * (size_t)p.n * p.n_sem, st);
-    if (p.n_tiles > 0 && p.n > 0) {
+    if (p.n_tiles > 0 && p.n > 0 && bwd_tc_selected(p)) {
+        launches += launch_render_bwd_tc(p, g, ws, fwd, go, grads, grec, st);
+    } else if (p.n_tiles > 0 && p.n > 0) {
         BwdParams P;
         P.tab = ws_ptr<CamTable>(ws, p, OFF_CAM);
         P.n_cams = p.n_cams;

@@ -436,9 +436,17 @@ static void launch_fwd_tc_f(const FwdTcParams& P, int batch, int grid, cudaStrea
     }
 }
 
+static bool fwd_tc_plan(const unigs_plan& p) {
+    return p.n_sem >= 9 && p.n_sem <= UNIGS_MAX_SEM && !(p.cfg.flags & UNIGS_FLAG_SIMT_LOGITS);
+}
+
 bool fwd_tc_eligible(const unigs_plan& p, const unigs_gaussians& g) {
-    return p.n_sem >= 9 && p.n_sem <= UNIGS_MAX_SEM && g.sem != nullptr &&
-           !(p.cfg.flags & UNIGS_FLAG_SIMT_LOGITS);
+    return fwd_tc_plan(p) && g.sem != nullptr;
+}
+
+bool sem32_needed(const unigs_plan& p) {
+    if (!p.feat_dtype || p.n_sem <= 0 || p.n <= 0) return false;
+    return !(fwd_tc_plan(p) && bwd_tc_selected(p));
 }
 
 int launch_render_fwd_tc(const unigs_plan& p, const unigs_gaussians& g, void* ws,

@@ -24,6 +24,11 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(const void* p, uint32_t lbo
     return d;
 }
 
+// The same descriptor fields describe an MN-major operand without swizzle
+// (core matrices of 8 K-rows x 16 bytes along M or N): lbo is again the byte
+// distance between core matrices adjacent along K and sbo between those
+// adjacent along M (or N).
+
 // Instruction descriptor of kind::f16 with bfloat16 A and B, float32
 // accumulation, both operands K-major, dense: D format (bits 4-5) = F32, A and
 // B formats (7-9, 10-12) = BF16, N >> 3 (17-22), M >> 4 (24-28).
@@ -31,6 +36,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
+// The same with float16 A and B (format 0).
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Operand-major bits of the instruction descriptor: A (bit 15) or B (bit 16)
+// stored MN-major.
+constexpr uint32_t IDESC_A_MN = 1u << 15;
+constexpr uint32_t IDESC_B_MN = 1u << 16;
 
 // Tensor-memory allocation of ncols columns (a power of two >= 32) by one
 // whole warp; the base address is written to *dst (shared memory).
@@ -95,6 +108,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One float32 column of this thread's tensor-memory lane.
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// 8 consecutive float32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace unigs

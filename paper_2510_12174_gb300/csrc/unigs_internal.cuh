@@ -14,7 +14,7 @@ constexpr int TILE_PIX = UNIGS_TILE_PIXELS;  // pixels of every tile shape
 
 // ----------------------------------------------------------------------------
 // Per-(camera, Gaussian) forward record written by the preprocess and staged
-// into shared memory by the composite kernels (48 floats = 192 bytes, a
+// into shared memory by the composite kernels (52 floats = 208 bytes, a
 // multiple of 16 so a bulk copy can move it).  The fields every evaluated
 // (pixel, Gaussian) pair reads (warp box test and alpha) fill the first three
 // 16-byte words.
@@ -42,11 +42,16 @@ constexpr int TILE_PIX = UNIGS_TILE_PIXELS;  // pixels of every tile shape
 //           from the camera
 //   [47]    3-sigma radius r of the binning recipe (pixels): the Gaussian is
 //           drawn only where |dx| <= r and |dy| <= r
+//   [48..49] (cos theta, sin theta): the principal axes e0 = (cos, sin),
+//           e1 = (-sin, cos) of the 2D covariance, the frame in which the
+//           backward records the covariance gradient
+//   [50..51] unused (zero)
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_CON = 4, R_OP = 7, R_EXTX = 8, R_EXTY = 9,
     R_FLAG = 10, R_SR = 11, R_MC = 12, R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34,
-    R_K = 37, R_RGB = 38, R_P1 = 41, R_P2 = 44, R_R3 = 47, REC_FLOATS = 48
+    R_K = 37, R_RGB = 38, R_P1 = 41, R_P2 = 44, R_R3 = 47, R_EC = 48, R_ES = 49,
+    REC_FLOATS = 52
 };
 
 // Pixel of thread tid inside its tile of width tw (8, 16, 32 or 64; 256
@@ -82,8 +87,9 @@ constexpr float KAPPA_FF = 64.f;
 // Per-(camera, Gaussian) intermediate gradient record (32 float64
 // accumulators, 256 bytes), filled by atomics in the backward composite and
 // consumed by the preprocess backward:
-// dL/d(projected centre x, y), dL/d(a, b, c) of the 2D covariance
-// [[a, b], [b, c]] (low-pass included), opacity, RGB, the local-frame matrix
+// dL/d(projected centre x, y), dL/d(a', b', c') of the 2D covariance
+// E^T [[a, b], [b, c]] E = [[a', b'], [b', c']] in the splat's principal frame
+// E (low-pass included; see the record's [48..49]), opacity, RGB, the local-frame matrix
 // B = sum g_vs (x) v_s + g_ds (x) d_s (row-major, accumulated as
 // g_vs (x) w + (g_ds - t g_vs) (x) d_s, see the backward composite), v_s, N_w,
 // k and the centre depth (centre-depth mode).

@@ -161,3 +161,38 @@ def test_launch_shape_fields_are_validated(lib):
         setattr(cfg, field, value)
         want = lib.UNIGS_OK if ok else lib.UNIGS_ERR_INVALID_ARG
         assert lib.unigs_plan_init(plan, g, arr, 1, cfg, 0) == want, (field, value)
+
+
+def test_plan_paths_select_the_composite_kernels(lib):
+    """unigs_plan_paths: which composites a plan runs, decided on the host from
+    the logit width, the feature dtype, the SIMT flag and the launch shapes;
+    the float32 logit copy (and its workspace) only where an FP32-pipe
+    composite reads bfloat16 rows."""
+    from paper_2510_12174_gb300 import rasterizer as rz, scenes
+    sc, cams = scenes.small_room(n=10, width=20, height=20)
+    arr = rz.make_cameras(cams)
+    FWD, BWD, S32 = lib.UNIGS_PATH_FWD_TC, lib.UNIGS_PATH_BWD_TC, lib.UNIGS_PATH_SEM32
+
+    def paths(n_sem, bf16, flags=0, batch=0, ctas=0):
+        g = lib.unigs_gaussians()
+        g.n, g.sh_degree, g.n_sem, g.feat_dtype = 1000, 3, n_sem, 1 if bf16 else 0
+        cfg = lib.unigs_config_default()
+        cfg.flags |= flags
+        cfg.batch, cfg.ctas_per_sm = batch, ctas
+        plan = lib.unigs_plan()
+        assert lib.unigs_plan_init(plan, g, arr, 1, cfg, 0) == lib.UNIGS_OK
+        return lib.unigs_plan_paths(plan), plan.ws_bytes
+
+    p, ws_tc = paths(64, True)
+    assert p == FWD | BWD
+    p, ws_simt = paths(64, True, batch=8, ctas=3)
+    assert p == FWD | S32
+    assert ws_simt - ws_tc >= 4 * 1000 * 64  # the float32 copy of the rows
+    assert paths(64, True, batch=16, ctas=2)[0] == FWD | BWD
+    assert paths(64, True, batch=16, ctas=3)[0] == FWD | S32
+    assert paths(64, True, flags=lib.UNIGS_FLAG_SIMT_LOGITS)[0] == S32
+    assert paths(64, False)[0] == FWD
+    assert paths(9, True)[0] == FWD | BWD
+    assert paths(8, True)[0] == S32
+    assert paths(0, True)[0] == 0
+    assert lib.lib().unigs_plan_paths(None) == 0

@@ -200,3 +200,73 @@ def test_local_frame_gradient_record_identities():
         assert np.allclose(cv_ds - t * cv_vs, np.cross(g_cv, w), rtol=1e-9,
                            atol=1e-9 * np.abs(cv_ds).max())
         n_done += 1
+
+
+def test_principal_frame_ewa_gradient_identities():
+    """The EWA part of the preprocess backward as the kernels evaluate it.
+
+    The gradient record holds G' = E^T G E, the gradient of the 2D covariance
+    cov = T Sigma T^T + lowpass I (T = J W, Sigma = R S^2 R^T) in the splat's
+    principal frame E (e0 at theta = atan2(2 c01, c00 - c11) / 2).  With
+    V' = E^T T R S and H = V'^T G' V', the kernels take
+      dL/ds_b = 2 H_bb / s_b,
+      dL/dtheta_k = 2 (s_i / s_j - s_j / s_i) H_ij   for (i, j, k) cyclic,
+      dL/dT = 2 E (G' V') (R S)^T,
+    then J's dependence on the camera-frame centre.  All must equal the
+    exact derivative of <G, cov> (rotation R -> R exp([theta]_x))."""
+    import torch
+    rng = np.random.default_rng(72)
+    for _ in range(30):
+        R0 = _rot(rng.normal(size=4))
+        W = _rot(rng.normal(size=4))
+        s = np.exp(rng.normal(-2.5, 1.0, size=3))
+        fx, fy = rng.uniform(200, 1500, size=2)
+        pc0 = np.array([rng.normal() * 3, rng.normal() * 3, rng.uniform(0.2, 5.0)])
+        Gm = rng.normal(size=(2, 2))
+        Gm = Gm + Gm.T
+        T_ = lambda x: torch.as_tensor(x, dtype=torch.float64)
+        th = torch.zeros(3, dtype=torch.float64, requires_grad=True)
+        st = T_(s).requires_grad_(True)
+        pc = T_(pc0).requires_grad_(True)
+        Kx = torch.zeros(3, 3, dtype=torch.float64).index_put(
+            (torch.tensor([0, 0, 1, 1, 2, 2]), torch.tensor([1, 2, 0, 2, 0, 1])),
+            torch.stack([-th[2], th[1], th[2], -th[0], -th[1], th[0]]))
+        R = T_(R0) @ torch.linalg.matrix_exp(Kx)
+        Sig = R @ torch.diag(st * st) @ R.T
+        x, y, z = pc[0], pc[1], pc[2]
+        zero = torch.zeros((), dtype=torch.float64)
+        J = torch.stack([torch.stack([fx / z, zero, -fx * x / (z * z)]),
+                         torch.stack([zero, fy / z, -fy * y / (z * z)])])
+        T = J @ T_(W)
+        cov = T @ Sig @ T.T + 0.3 * torch.eye(2, dtype=torch.float64)
+        L = (T_(Gm) * cov).sum()
+        g_th, g_s, g_pc = torch.autograd.grad(L, (th, st, pc))
+        # the kernels' evaluation
+        cv = cov.detach().numpy()
+        ang = 0.5 * np.arctan2(2 * cv[0, 1], cv[0, 0] - cv[1, 1])
+        ec, es = np.cos(ang), np.sin(ang)
+        E = np.array([[ec, -es], [es, ec]])
+        Gp = E.T @ Gm @ E
+        Tn = T.detach().numpy()
+        M = R0 * s[None, :]
+        Vp = (E.T @ Tn) @ M
+        GV = Gp @ Vp
+        H = Vp.T @ GV
+        gs_k = 2 * np.diag(H) / s
+        gth_k = np.array([2 * (s[1] / s[2] - s[2] / s[1]) * H[1, 2],
+                          2 * (s[2] / s[0] - s[0] / s[2]) * H[2, 0],
+                          2 * (s[0] / s[1] - s[1] / s[0]) * H[0, 1]])
+        gT = 2 * (E @ GV) @ M.T
+        gJ = gT @ W.T
+        iz = 1 / pc0[2]
+        gpc_k = np.array([
+            gJ[0, 2] * (-fx * iz * iz), gJ[1, 2] * (-fy * iz * iz),
+            -gJ[0, 0] * fx * iz * iz + gJ[0, 2] * 2 * fx * pc0[0] * iz ** 3
+            - gJ[1, 1] * fy * iz * iz + gJ[1, 2] * 2 * fy * pc0[1] * iz ** 3])
+        sc = lambda v: 1e-9 * (1 + np.abs(v).max())
+        assert np.allclose(gs_k, g_s.numpy(), rtol=1e-9, atol=sc(g_s.numpy()))
+        assert np.allclose(gth_k, g_th.numpy(), rtol=1e-9, atol=sc(g_th.numpy()))
+        assert np.allclose(gpc_k, g_pc.numpy(), rtol=1e-9, atol=sc(g_pc.numpy()))
+        # E diagonalises the 2D covariance (the frame the record is kept in)
+        d = E.T @ cv @ E
+        assert abs(d[0, 1]) < 1e-9 * np.abs(cv).max()
