@@ -263,20 +263,23 @@ def alpha_error_bound(con: torch.Tensor, dx: torch.Tensor, dy: torch.Tensor,
     of the absolute terms of q) and u = 2^-24:
       * float32 quadratic form (kappa <= KAPPA_SPLIT): rounding the conic to
         float32 and the three products and two additions give
-        |dq| <= 4 u S (6 u S taken); double-float form otherwise: |dq| <= u q
-        (the final rounding);
+        |dq| <= 4 u S (6 u S taken); otherwise the conditional form
+        q = P w^2 + e b^2 with w = a + rho b formed from the exact offset by
+        an error-free product and sum (rounded once) and P, e rounded to
+        float32: each non-negative term carries 5 u (its inputs and two
+        products) and the sum one more, |dq| <= 6 u q;
       * exp(-q/2) then carries a relative error q/2 * |dq|/q, plus q u from
         the rounded product x log2(e) inside the hardware exp, plus the exp2
         approximation (2^-21 taken);
       * the product with the opacity rounds once more (u).
     So beta = u (3 S + q + 1) + 2^-21 on the float32 path and
-    u (1.5 q + 1) + 2^-21 on the double-float path."""
+    u (4 q + 1) + 2^-21 on the conditional-form path."""
     q = con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy + 2.0 * con[None, :, 1] * dx * dy
     S = con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy \
         + 2.0 * (con[None, :, 1] * dx * dy).abs()
     f32_path = (kappa <= KAPPA_SPLIT)[None, :]
     beta32 = U32 * (3.0 * S + q + 1.0)
-    betaff = U32 * (1.5 * q + 1.0)
+    betaff = U32 * (4.0 * q + 1.0)
     return torch.where(f32_path, beta32, betaff) + EXP2_APPROX
 
 

@@ -38,10 +38,10 @@ __device__ __forceinline__ void cross_acc(const float* a, const float* b, float*
 // Restores T across the Gaussian (T <- T / (1 - alpha)) where the pixel
 // contributes, advances Sacc and fills the pair's 32-entry gradient vector gv
 // (every entry zero where it does not: w = 0 and dL/dalpha = 0, all
-// intermediates finite).  alpha, (dx, dy) and Gs come from splat_alpha.
+// intermediates finite).  alpha, (dx, dy), Gs and wq come from splat_alpha.
 // Returns w (0 where the pixel does not contribute).
 __device__ __forceinline__ float bwd_pair(const float* __restrict__ rc, const PixelUp& up,
-                                          float xt, float yt, float uf, float vf, float dx,
+                                          float xt, float yt, float wq, float dx,
                                           float dy, float alpha, float Gs, bool contrib,
                                           float G_sem, float alpha_max, int center_depth,
                                           float& T, float& Sacc, float (&gv)[32]) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ float bwd_pair(const float* __restrict__ rc, const Pi
     gv[G_OP] = clamped ? 0.f : dL_da * Gs;
     // power = -1/2 D^T K D: dL/dm = g u, dL/dcov = g/2 u u^T, u = K D
     float kux, kuy;
-    splat_kdelta(rc, uf, vf, dx, dy, &kux, &kuy);
+    splat_kdelta(rc, dx, dy, wq, &kux, &kuy);
     {
         // dL/dcov = 1/2 g u u^T, recorded in the splat's principal frame E
         // (u' = E^T u): in the pixel frame the entries of a thin splat seen far

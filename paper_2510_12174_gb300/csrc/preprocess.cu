@@ -141,6 +141,11 @@ struct SplatFF {
     float kappa;
     float cxx, cyy;  // diagonal of the 2D covariance
     float ec, es;    // principal axis e0 = (ec, es) of the 2D covariance
+    // conditional form of the quadratic, q = P (a + rho b)^2 + e b^2 with the
+    // pivot coordinate a = x when c11 > c00 (piv_x), else a = y
+    float P, e;
+    ff rho;
+    bool piv_x;
 };
 
 __device__ __forceinline__ void split_center(ff m, float* hi, float* lo) {
@@ -173,6 +178,14 @@ __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy
     o.A = ff_div(c11, det);
     o.B = ff_neg(ff_div(c01, det));
     o.C = ff_div(c00, det);
+    // pivot on the coordinate with the larger conic diagonal: for a = y,
+    // P = c00 / det, rho = -c01 / c00 (|rho| <= 1), e = 1 / c00 (only P
+    // carries the determinant's cancellation, held in double-float)
+    o.piv_x = ff_val(c11) > ff_val(c00);
+    const ff cp = o.piv_x ? c11 : c00;
+    o.P = ff_val(ff_div(cp, det));
+    o.rho = ff_neg(ff_div(c01, cp));
+    o.e = __frcp_rn(ff_val(cp));
     split_center(ff_add(ff_mul_f(xz, cam.fx), ff_from(cam.cx)), &o.mxh, &o.mxl);
     split_center(ff_add(ff_mul_f(yz, cam.fy), ff_from(cam.cy)), &o.myh, &o.myl);
     // eigenvalue ratio of the conic: lmax^2 / det(conic)
@@ -293,13 +306,22 @@ __global__ void __launch_bounds__(256)
         o[R_MYL] = sf.myl;
         o[R_OP] = __ldg(g.opacity + i);
         o[R_K] = __ldg(g.kfac + i);
-        o[R_CON + 0] = sf.A.hi;
-        o[R_CON + 1] = sf.B.hi;
-        o[R_CON + 2] = sf.C.hi;
-        o[R_CLO + 0] = sf.A.lo;
-        o[R_CLO + 1] = sf.B.lo;
-        o[R_CLO + 2] = sf.C.lo;
         o[R_FLAG] = sf.kappa > KAPPA_FF ? 1.f : 0.f;
+        if (o[R_FLAG] != 0.f) {
+            // ill-conditioned: the conditional form (see splat_alpha)
+            o[R_CON + 0] = sf.P;
+            o[R_CON + 1] = sf.rho.hi;
+            o[R_CON + 2] = sf.rho.lo;
+            o[R_CLO + 0] = sf.e;
+            o[R_CLO + 1] = sf.piv_x ? 1.f : 0.f;
+        } else {
+            o[R_CON + 0] = sf.A.hi;
+            o[R_CON + 1] = sf.B.hi;
+            o[R_CON + 2] = sf.C.hi;
+            o[R_CLO + 0] = 0.f;
+            o[R_CLO + 1] = 0.f;
+        }
+        o[R_CLO + 2] = 0.f;
         o[R_EC] = sf.ec;
         o[R_ES] = sf.es;
         o[R_ES + 1] = o[R_ES + 2] = 0.f;

@@ -276,12 +276,12 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
                 // some lane contributes, and then as a whole: a lane that does not
                 // contribute carries w = 0 and dL/dalpha = 0, which makes every
                 // entry of its gradient vector zero (all intermediates are finite)
-                float dx, dy, Gs;
-                const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                float dx, dy, Gs, wq;
+                const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs, &wq);
                 const bool contrib = !timed_out && pos < last && alpha >= P.alpha_min;
                 if (!__any_sync(0xffffffffu, contrib)) continue;
                 float gv[32];
-                const float w = bwd_pair(rc, up, xt, yt, uf, vf, dx, dy, alpha, Gs, contrib,
+                const float w = bwd_pair(rc, up, xt, yt, wq, dx, dy, alpha, Gs, contrib,
                                          sem_dot<NS>(a_row, &S.sem[buf][j][0]), P.alpha_max,
                                          P.center_depth, T, Sacc, gv);
                 {

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
                     if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
                     if (done) continue;
                     float dx, dy, Gs;
-                    const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs);
+                    float wq;
+                    const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs, &wq);
                     ++n_eval;
                     if (alpha < P.alpha_min) continue;
                     const float test_T = T * (1.f - alpha);

@@ -12,30 +12,38 @@ namespace unigs {
 // gets -1, below every alpha_min: the Gaussian is not drawn there (the tiles
 // of the binning only have to cover the square, so the image does not depend
 // on the tile shape).  Ill-conditioned splats (flag set by the preprocess)
-// evaluate the quadratic form in double-float from the double-float conic;
-// the branch is uniform across a CTA because all its threads walk the same
+// take D exactly as a double-float pair and the quadratic form in its
+// conditional form q = P w^2 + e b^2, w = a + rho b (a the pivot coordinate,
+// see the record): both terms are non-negative, so only w needs an
+// error-free product and sum, where A dx^2 + 2 B dx dy + C dy^2 cancels along
+// the long axis; *w_out returns w for splat_kdelta (0 on the float path).
+// The branch is uniform across a CTA because all its threads walk the same
 // Gaussian.  Written with non-contractible intrinsics so the forward and the
 // backward (which recomputes alpha to undo T) obtain the same bits.
 __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float uf, float vf,
                                              float alpha_max, float* dx_out, float* dy_out,
-                                             float* gauss_out) {
+                                             float* gauss_out, float* w_out) {
     const float ux = __fsub_rn(uf, rc[R_MXH]);  // exact (integers)
     const float vy = __fsub_rn(vf, rc[R_MYH]);
     const float r3 = rc[R_R3];
-    float q;
+    float q, w = 0.f;
     bool outside;
     if (rc[R_FLAG] != 0.f) {
-        const ff dx = two_sum(ux, -rc[R_MXL]);
-        const ff dy = two_sum(vy, -rc[R_MYL]);
-        *dx_out = ff_val(dx);
-        *dy_out = ff_val(dy);
-        outside = fmaxf(fabsf(*dx_out), fabsf(*dy_out)) > r3;
-        const ff A = {rc[R_CON], rc[R_CLO]}, B = {rc[R_CON + 1], rc[R_CLO + 1]},
-                 C = {rc[R_CON + 2], rc[R_CLO + 2]};
-        const ff t1 = ff_mul(A, ff_mul(dx, dx));
-        const ff t2 = ff_scale(ff_mul(B, ff_mul(dx, dy)), 2.f);
-        const ff t3 = ff_mul(C, ff_mul(dy, dy));
-        q = ff_val(ff_add(ff_add(t1, t2), t3));
+        // |ux| >= 1 > |remainder| or ux = 0: the fast transformation is exact
+        const ff dx = fast_two_sum(ux, -rc[R_MXL]);
+        const ff dy = fast_two_sum(vy, -rc[R_MYL]);
+        *dx_out = dx.hi;
+        *dy_out = dy.hi;
+        outside = fmaxf(fabsf(dx.hi), fabsf(dy.hi)) > r3;
+        const bool piv_x = rc[R_CLO + 1] != 0.f;
+        const ff a = piv_x ? dx : dy, b = piv_x ? dy : dx;
+        const float rh = rc[R_CON + 1], rl = rc[R_CON + 2];
+        const ff p = two_prod(rh, b.hi);
+        const ff sm = two_sum(a.hi, p.hi);
+        const float tail = __fadd_rn(__fadd_rn(sm.lo, p.lo),
+                                     __fmaf_rn(rh, b.lo, __fmaf_rn(rl, b.hi, a.lo)));
+        w = __fadd_rn(sm.hi, tail);
+        q = __fmaf_rn(__fmul_rn(rc[R_CON], w), w, __fmul_rn(__fmul_rn(rc[R_CLO], b.hi), b.hi));
     } else {
         const float dx = __fsub_rn(ux, rc[R_MXL]);
         const float dy = __fsub_rn(vy, rc[R_MYL]);
@@ -46,6 +54,7 @@ __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float
         q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(__fmul_rn(C, dy), dy)),
                       __fmul_rn(2.f, __fmul_rn(__fmul_rn(B, dx), dy)));
     }
+    *w_out = w;
     // the square test is applied as a select, after the exponential, so the
     // warp does not diverge ahead of it
     const float G = __expf(__fmul_rn(-0.5f, q));
@@ -54,18 +63,17 @@ __device__ __forceinline__ float splat_alpha(const float* __restrict__ rc, float
 }
 
 // u = K D (conic times pixel offset), the direction of every alpha gradient:
-// dL/dm = g u and dL/dcov = g/2 u u^T for g = dL/dpower.  Flagged
-// (ill-conditioned) splats form it in double-float, because K D cancels along
-// the long axis exactly like the quadratic form does.
-__device__ __forceinline__ void splat_kdelta(const float* __restrict__ rc, float uf, float vf,
-                                             float dx, float dy, float* ux, float* uy) {
+// dL/dm = g u and dL/dcov = g/2 u u^T for g = dL/dpower.  For an
+// ill-conditioned splat from the conditional form (the gradient of q/2):
+// u_a = P w, u_b = P w rho + e b, with w from splat_alpha.
+__device__ __forceinline__ void splat_kdelta(const float* __restrict__ rc, float dx, float dy,
+                                             float w, float* ux, float* uy) {
     if (rc[R_FLAG] != 0.f) {
-        const ff fdx = two_sum(__fsub_rn(uf, rc[R_MXH]), -rc[R_MXL]);
-        const ff fdy = two_sum(__fsub_rn(vf, rc[R_MYH]), -rc[R_MYL]);
-        const ff A = {rc[R_CON], rc[R_CLO]}, B = {rc[R_CON + 1], rc[R_CLO + 1]},
-                 C = {rc[R_CON + 2], rc[R_CLO + 2]};
-        *ux = ff_val(ff_add(ff_mul(A, fdx), ff_mul(B, fdy)));
-        *uy = ff_val(ff_add(ff_mul(B, fdx), ff_mul(C, fdy)));
+        const bool piv_x = rc[R_CLO + 1] != 0.f;
+        const float ua = rc[R_CON] * w;
+        const float ub = fmaf(ua, rc[R_CON + 1], rc[R_CLO] * (piv_x ? dy : dx));
+        *ux = piv_x ? ua : ub;
+        *uy = piv_x ? ub : ua;
     } else {
         *ux = fmaf(rc[R_CON], dx, rc[R_CON + 1] * dy);
         *uy = fmaf(rc[R_CON + 1], dx, rc[R_CON + 2] * dy);

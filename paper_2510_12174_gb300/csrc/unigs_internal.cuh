@@ -20,7 +20,9 @@ constexpr int TILE_PIX = UNIGS_TILE_PIXELS;  // pixels of every tile shape
 // 16-byte words.
 //   [0..3]  projected centre split as integer part + remainder (x_hi, y_hi,
 //           x_lo, y_lo); m = hi + lo, hi an integer-valued float, |lo| <= 0.5
-//   [4..6]  conic (A, B, C) of the inverse 2D covariance (high words)
+//   [4..6]  conic (A, B, C) of the inverse 2D covariance; for an
+//           ill-conditioned splat (flag [10]) instead the conditional form
+//           q = P (a + rho b)^2 + e b^2: (P, rho_hi, rho_lo)
 //   [7]     opacity
 //   [8..9]  half-extents (x, y) of the box holding every pixel where alpha
 //           can reach alpha_min (with margin): a warp whose 8x4 pixel block
@@ -33,7 +35,8 @@ constexpr int TILE_PIX = UNIGS_TILE_PIXELS;  // pixels of every tile shape
 //   [21..23] v_s = S^-1 R^T (C - mu)
 //   [24..32] N_w = R S^-1 (scaled-local normal -> world), row-major
 //   [33]    camera-frame z of the centre
-//   [34..36] low words of the conic (double-float A, B, C)
+//   [34..36] ill-conditioned splat: e, pivot (1: a = x, b = y; 0: a = y,
+//           b = x), 0; else 0
 //   [37]    k (gradient factor)
 //   [38..40] RGB
 //   [41..43] P1, [44..46] P2: v_s x d_s = dx P1 + dy P2 for the pixel offset

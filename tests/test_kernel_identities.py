@@ -270,3 +270,37 @@ def test_principal_frame_ewa_gradient_identities():
         # E diagonalises the 2D covariance (the frame the record is kept in)
         d = E.T @ cv @ E
         assert abs(d[0, 1]) < 1e-9 * np.abs(cv).max()
+
+
+def test_conditional_form_of_the_quadratic():
+    """The double-float alpha path of ill-conditioned splats evaluates
+    q = D^T K D (K = cov^-1) in the conditional (LDL^T) form the preprocess
+    records: pivot on y when c00 >= c11,
+      q = P (dy + rho dx)^2 + e dx^2,  P = c00 / det, rho = -c01 / c00,
+      e = 1 / c00,
+    on x otherwise (the roles of x and y swapped), and u = K D from the same
+    quantities: u_pivot = P w, u_other = P w rho + e b.  Exact in float64 for
+    every conditioning, including the near-singular covariances that send a
+    splat down that path."""
+    rng = np.random.default_rng(73)
+    for _ in range(2000):
+        th = rng.uniform(0, np.pi)
+        l1, l2 = np.exp(rng.uniform(-2, 12, size=2))
+        E = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        cov = E @ np.diag([l1, l2]) @ E.T + 0.3 * np.eye(2)
+        c00, c01, c11 = cov[0, 0], cov[0, 1], cov[1, 1]
+        det = c00 * c11 - c01 * c01
+        K = np.linalg.inv(cov)
+        D = rng.normal(size=2) * np.sqrt(max(l1, l2)) * 3
+        piv_x = c11 > c00
+        cp = c11 if piv_x else c00
+        P, rho, e = cp / det, -c01 / cp, 1.0 / cp
+        a, b = (D[0], D[1]) if piv_x else (D[1], D[0])
+        w = a + rho * b
+        q = P * w * w + e * b * b
+        q_ref = D @ K @ D
+        assert abs(q - q_ref) <= 1e-9 * abs(q_ref) + 1e-12
+        assert abs(rho) <= 1.0 + 1e-15 and P > 0 and e > 0
+        ua, ub = P * w, P * w * rho + e * b
+        u = np.array([ua, ub]) if piv_x else np.array([ub, ua])
+        assert np.allclose(u, K @ D, rtol=1e-9, atol=1e-12 * np.abs(K @ D).max())
