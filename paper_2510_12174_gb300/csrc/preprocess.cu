@@ -141,6 +141,7 @@ struct SplatFF {
     float kappa;
     float cxx, cyy;  // diagonal of the 2D covariance
     float ec, es;    // principal axis e0 = (ec, es) of the 2D covariance
+    float lam0, lam1;  // its eigenvalues along e0 (the larger) and e1
     // conditional form of the quadratic, q = P (a + rho b)^2 + e b^2 with the
     // pivot coordinate a = x when c11 > c00 (piv_x), else a = y
     float P, e;
@@ -175,6 +176,11 @@ __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy
     // orthonormal pair is a valid frame; this one keeps the recorded
     // covariance gradient free of cancellation for thin splats)
     sincosf(0.5f * atan2f(2.f * ff_val(c01), ff_val(ff_sub(c00, c11))), &o.es, &o.ec);
+    {
+        const float hd = 0.5f * ff_val(ff_sub(c00, c11)), co = ff_val(c01);
+        o.lam0 = 0.5f * (ff_val(c00) + ff_val(c11)) + sqrtf(hd * hd + co * co);
+        o.lam1 = ff_val(det) / o.lam0;
+    }
     o.A = ff_div(c11, det);
     o.B = ff_neg(ff_div(c01, det));
     o.C = ff_div(c00, det);
@@ -324,7 +330,6 @@ __global__ void __launch_bounds__(256)
         o[R_CLO + 2] = 0.f;
         o[R_EC] = sf.ec;
         o[R_ES] = sf.es;
-        o[R_ES + 1] = o[R_ES + 2] = 0.f;
 
         // colour from SH, viewing direction mu - C
         float dx = mux - cam.C[0], dy = muy - cam.C[1], dz = muz - cam.C[2];
@@ -397,6 +402,9 @@ __global__ void __launch_bounds__(256)
             const float sq = rc.radius + 0.01f;
             o[R_EXTX] = fminf(sqrtf(ql * sf.cxx) * 1.01f + 1.f, sq);
             o[R_EXTY] = fminf(sqrtf(ql * sf.cyy) * 1.01f + 1.f, sq);
+            // the same ellipse's half-extents along its principal axes
+            o[R_E0] = sqrtf(ql * sf.lam0) * 1.01f + 1.f;
+            o[R_E1] = sqrtf(ql * fmaxf(sf.lam1, 0.f)) * 1.01f + 1.f;
         }
         float4* dst = reinterpret_cast<float4*>(rec + (size_t)t * REC_FLOATS);
 #pragma unroll

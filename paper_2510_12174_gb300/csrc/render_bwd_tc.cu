@@ -461,11 +461,14 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_CTAS_PER_SM)
                         const uint32_t pos = (uint32_t)(b * B + j);
                         const float* rc = &S.rec[bf][j][0];
                         if (warp_block_misses(rc, bx0, by0)) continue;  // uniform per warp
+                        // Gsem of this pixel and Gaussian, loaded while alpha is evaluated
+                        const uint32_t gsem_raw = tmem_ld1_issue(d1 + (uint32_t)j);
                         float dx, dy, Gs, wq;
                         const float alpha = splat_alpha(rc, uf, vf, P.alpha_max, &dx, &dy, &Gs, &wq);
+                        const float gsem = tmem_ld1_wait(gsem_raw);
                         const bool contrib = !timed_out && pos < last && alpha >= P.alpha_min;
                         if (!__any_sync(0xffffffffu, contrib)) continue;
-                        const float G_sem = tmem_ld1(d1 + (uint32_t)j) * ginv * finv;
+                        const float G_sem = gsem * ginv * finv;
                         float gv[32];
                         const float w = bwd_pair(rc, up, xt, yt, wq, dx, dy, alpha, Gs,
                                                  contrib, G_sem, P.alpha_max, P.center_depth, T,

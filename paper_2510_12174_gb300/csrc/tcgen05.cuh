@@ -118,6 +118,19 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     return __uint_as_float(r);
 }
 
+// A tensor-memory load issued early and waited for later: the wait takes the
+// destination register as an operand, so it stays allocated (and is not read)
+// until the load has landed.
+__device__ __forceinline__ uint32_t tmem_ld1_issue(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return r;
+}
+__device__ __forceinline__ float tmem_ld1_wait(uint32_t r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r)::"memory");
+    return __uint_as_float(r);
+}
+
 // 8 consecutive float32 columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r[8];

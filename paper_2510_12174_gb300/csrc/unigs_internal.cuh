@@ -48,13 +48,15 @@ constexpr int TILE_PIX = UNIGS_TILE_PIXELS;  // pixels of every tile shape
 //   [48..49] (cos theta, sin theta): the principal axes e0 = (cos, sin),
 //           e1 = (-sin, cos) of the 2D covariance, the frame in which the
 //           backward records the covariance gradient
-//   [50..51] unused (zero)
+//   [50..51] half-extents along e0 and e1 of the ellipse holding every pixel
+//           where alpha can reach alpha_min (with margin): with [8..9] the
+//           two boxes of the warp-block skip test
 // ----------------------------------------------------------------------------
 enum {
     R_MXH = 0, R_MYH, R_MXL, R_MYL, R_CON = 4, R_OP = 7, R_EXTX = 8, R_EXTY = 9,
     R_FLAG = 10, R_SR = 11, R_MC = 12, R_VS = 21, R_NW = 24, R_Z = 33, R_CLO = 34,
     R_K = 37, R_RGB = 38, R_P1 = 41, R_P2 = 44, R_R3 = 47, R_EC = 48, R_ES = 49,
-    REC_FLOATS = 52
+    R_E0 = 50, R_E1 = 51, REC_FLOATS = 52
 };
 
 // Pixel of thread tid inside its tile of width tw (8, 16, 32 or 64; 256
@@ -75,12 +77,22 @@ __device__ __forceinline__ void warp_block(int w, int tw, int* bx, int* by) {
 }
 
 // True when the Gaussian cannot reach alpha_min anywhere in the warp's block
-// [bx0, bx0+7] x [by0, by0+3] (uniform across the warp).
+// [bx0, bx0+7] x [by0, by0+3] (uniform across the warp): the block lies
+// outside the axis-aligned box of the q <= qlim ellipse, or outside the box
+// along the ellipse's principal axes (separating-axis test of the block's
+// half-extents 3.5 x 1.5 projected on e0, e1), which for an elongated splat
+// is far smaller.
 __device__ __forceinline__ bool warp_block_misses(const float* __restrict__ rc, float bx0,
                                                   float by0) {
     const float mx = rc[R_MXH] + rc[R_MXL], my = rc[R_MYH] + rc[R_MYL];
     const float ex = rc[R_EXTX], ey = rc[R_EXTY];
-    return (bx0 + 7.f < mx - ex) || (bx0 > mx + ex) || (by0 + 3.f < my - ey) || (by0 > my + ey);
+    if ((bx0 + 7.f < mx - ex) || (bx0 > mx + ex) || (by0 + 3.f < my - ey) || (by0 > my + ey))
+        return true;
+    const float cx = bx0 + 3.5f - mx, cy = by0 + 1.5f - my;
+    const float c = rc[R_EC], s = rc[R_ES];
+    const float ac = fabsf(c), as = fabsf(s);
+    return fabsf(fmaf(c, cx, s * cy)) > rc[R_E0] + fmaf(3.5f, ac, 1.5f * as) ||
+           fabsf(fmaf(-s, cx, c * cy)) > rc[R_E1] + fmaf(3.5f, as, 1.5f * ac);
 }
 
 // Conic eigenvalue ratio above which alpha is evaluated in double-float: the
