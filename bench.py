@@ -112,14 +112,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one render_bwd launch on this workload, from a
-# one-pass ncu capture of the full run (dram__bytes_read.sum 7.02 GB +
-# dram__bytes_write.sum 1.12 GB; the metrics take one pass on the small
-# profiling case too), valid only for the kernel sources whose digest is
-# recorded here; any change to them reports null until re-captured.
-BWD_TRAFFIC_BYTES = 8_140_000_000
-BWD_TRAFFIC_SOURCES = ('render_bwd.cu', 'splat.cuh', 'unigs_internal.cuh', 'ff.cuh', 'sh.cuh')
-BWD_TRAFFIC_DIGEST = "9634ff3710a701c5b4d07c4ffbc3fe454e785d9793ca374244ed1c972fb40447"
+# DRAM bytes (read + write) of one launch of the backward composite on this
+# workload (render_bwd_tc_kernel<64>), from a one-pass ncu capture of the
+# full run (dram__bytes_read.sum 6.809 GB + dram__bytes_write.sum 1.073 GB;
+# the two metrics take one pass), valid only for the kernel sources whose
+# digest is recorded here; any change to them reports null until re-captured.
+BWD_TRAFFIC_BYTES = 7_881_512_960
+BWD_TRAFFIC_SOURCES = ('render_bwd.cu', 'render_bwd_tc.cu', 'bwd_pair.cuh', 'splat.cuh',
+                       'unigs_internal.cuh', 'ff.cuh', 'sh.cuh', 'tcgen05.cuh', 'ewa_ff.cuh')
+BWD_TRAFFIC_DIGEST = "896620a59265594c543c23d08f1243fcfa12bf13773868dabfc003847f699a2b"
 
 
 def bwd_traffic():
@@ -147,16 +148,22 @@ def hbm_bytes_per_step(n: int, sh_degree: int, n_sem: int, pixels: int, instance
     return 2 * P + G + O + U + 44 * instances
 
 
-def launch_shape(cfg, simt_logits: bool) -> dict:
-    """The composites' launch shapes after the library's defaults."""
-    bwd = (int(cfg.batch) or 8, int(cfg.ctas_per_sm) or 3)
-    if simt_logits:
+def launch_shape(cfg, paths: int) -> dict:
+    """The composites' kernels and launch shapes after the library's defaults
+    (``paths``: unigs_plan_paths of the plan)."""
+    from paper_2510_12174_gb300 import abi
+    fwd_tc = bool(paths & abi.UNIGS_PATH_FWD_TC)
+    bwd_tc = bool(paths & abi.UNIGS_PATH_BWD_TC)
+    bwd = (16, 2) if bwd_tc else (int(cfg.batch) or 8, int(cfg.ctas_per_sm) or 3)
+    if not fwd_tc:
         fwd = (int(cfg.batch_fwd) or 32, int(cfg.ctas_per_sm_fwd) or 2)
     else:
         fwd = (int(cfg.batch_fwd) or 16, min(int(cfg.ctas_per_sm_fwd) or 4, 4))
     return {"tile": [int(cfg.tile_w) or 16, int(cfg.tile_h) or 16],
-            "fwd": {"batch": fwd[0], "ctas_per_sm": fwd[1]},
-            "bwd": {"batch": bwd[0], "ctas_per_sm": bwd[1]}}
+            "fwd": {"batch": fwd[0], "ctas_per_sm": fwd[1],
+                    "logits": "tensor cores" if fwd_tc else "fp32 pipes"},
+            "bwd": {"batch": bwd[0], "ctas_per_sm": bwd[1],
+                    "logits": "tensor cores" if bwd_tc else "fp32 pipes"}}
 
 
 def parse_tile(text: str) -> tuple:
@@ -223,8 +230,12 @@ def measure_fp32_peak(dev) -> dict:
 # from its source (FMA = 2): alpha recomputation ~24 per evaluated pair; per
 # blended pair ~ 80 (geometry recompute) + 2*(8 + n_sem) (G_i dot) + ~190
 # (alpha, depth, normal chains) + 2*n_sem (semantic gradients).
-def bwd_flops(n_eval, n_blend, n_sem):
-    return 24.0 * n_eval + (80 + 2 * (8 + n_sem) + 190 + 2 * n_sem) * n_blend
+def bwd_flops(n_eval, n_blend, n_sem, tensor_logits=False):
+    """FP32-pipe flops of the backward; with ``tensor_logits`` the 4 n_sem of
+    the logit terms (G_i's logit dot product and the logit-feature gradient)
+    run on the tensor cores and are not counted."""
+    sem = 0 if tensor_logits else 4 * n_sem
+    return 24.0 * n_eval + (80 + 16 + 190 + sem) * n_blend
 
 
 def fwd_flops(n_eval, n_blend, n_sem):
@@ -288,6 +299,7 @@ def measure_configs(dev, fp32_tflops: float, hbm_gbs: float, steps: int) -> dict
     (algorithmic bytes over the measured copy bandwidth)."""
     import torch
 
+    from paper_2510_12174_gb300 import abi
     from paper_2510_12174_gb300 import rasterizer as rz
     from paper_2510_12174_gb300 import scenes
 
@@ -378,6 +390,7 @@ def measure_configs(dev, fp32_tflops: float, hbm_gbs: float, steps: int) -> dict
     ch = {"rgb": 3, "depth": 1, "normal_g": 3, "kmap": 1, "logits": sc.n_sem, "normal_d": 3}
     up_views = [{k: up[k][offs[i] * c: offs[i + 1] * c] for k, c in ch.items()}
                 for i in range(len(cams))]
+    tc4 = bool(abi.unigs_plan_paths(rb.plan) & abi.UNIGS_PATH_BWD_TC)
     del rb, ob, gb, gbufb
     torch.cuda.empty_cache()
     ds32 = rz.DeviceScene.from_scene(sc, device=dev, feat_bf16=False)
@@ -393,7 +406,7 @@ def measure_configs(dev, fp32_tflops: float, hbm_gbs: float, steps: int) -> dict
     looped_ms = _time_ms(looped, max(2, n_rep // 2), 1, dev)
     pix = sum(c.width * c.height for c in cams)
     nbytes = hbm_bytes_per_step(sc.n, sc.sh_degree, sc.n_sem, pix, n_inst, 2)
-    flops = fwd_flops(n_eval, n_blend, sc.n_sem) + bwd_flops(n_eval, n_blend, sc.n_sem)
+    flops = fwd_flops(n_eval, n_blend, sc.n_sem) + bwd_flops(n_eval, n_blend, sc.n_sem, tc4)
     res["config4"] = {"workload": "3M Gaussians, 16 orbit views drawn from 640x480, 1280x720 "
                                   "and 1920x1080, 64 logits, SH3, forward + backward",
                       "batched_views_per_s": len(cams) * 1000.0 / batched_ms,
@@ -633,7 +646,8 @@ def run_ours(args):
 
     peaks, src = _peaks()
     clocks = clk.summary()
-    f_bwd = bwd_flops(n_eval, n_blend, n_sem)
+    paths = abi.unigs_plan_paths(r.plan)
+    f_bwd = bwd_flops(n_eval, n_blend, n_sem, bool(paths & abi.UNIGS_PATH_BWD_TC))
     bwd_ms = stage_ms[3]
     fp32 = measure_fp32_peak(dev)
     fp32_peak = fp32["tflops"]
@@ -645,15 +659,16 @@ def run_ours(args):
         "data": "synthetic",
         "config": workload_config(args.n_gauss),
         "run": {"path": "batched, one CUDA graph per step", "parallelism": f"replicas{world}",
-                "launch_shape": launch_shape(r.cfg, args.simt_logits),
-                "logit_blend": "fp32 pipes" if args.simt_logits else "tensor cores"},
+                "launch_shape": launch_shape(r.cfg, paths)},
         "per_view": pv,
         "stage_ms": {"preprocess+bin_sort": stage_ms[0], "render_fwd+normal_d": stage_ms[1],
                      "depth_normal_bwd": stage_ms[2], "render_bwd": stage_ms[3]},
         "work": {"pairs_evaluated": n_eval, "pairs_blended": n_blend,
                  "instances": n_inst,
                  "gaussian_pixel_evals_per_s": n_eval / (ms_all / 1000.0)},
-        "roofline": {"bound": "alu", "kernel": "render_bwd (composite backward + preprocess backward)",
+        "roofline": {"bound": "alu",
+                     "kernel": "render_bwd (composite backward + preprocess backward; the logit "
+                               "terms on the tensor cores where the plan runs them there)",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
                      "traffic": (bwd_traffic() if (args.n_gauss, args.batch, args.ctas) ==
@@ -661,8 +676,9 @@ def run_ours(args):
                      "peak_source": "measured: FP32 FMA probe (unigs_probe_fma) on this GPU, "
                                     "best of scalar and packed-pair FMAs",
                      "peak_probe": fp32,
-                     "flops_model": "per evaluated pair 24, per blended pair "
-                                    f"{80 + 2 * (8 + n_sem) + 190 + 2 * n_sem} (FMA = 2)"},
+                     "flops_model": "FP32-pipe flops: per evaluated pair 24, per blended pair "
+                                    f"{int(bwd_flops(0, 1, n_sem, bool(paths & abi.UNIGS_PATH_BWD_TC)))} "
+                                    "(FMA = 2)"},
         "e2e": {"value": N_VIEWS / (e2e_ms / 1000.0) * world, "unit": "views/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 64,
                 "note": "per step: targets (rgb, depth, normal, label) host->device from pinned "
