@@ -280,7 +280,10 @@ unigs_status unigs_depth_normal_bwd(const unigs_plan* plan, const unigs_camera* 
  * the per-Gaussian chain to mu, q (tangent projection of the normalised
  * quaternion), s, opacity, SH, k and the logits (supplement Sec. 2 for the
  * depth; the EWA and SH chain of 3DGS for the rest).  fwd must hold the
- * T_final / n_contrib of the matching unigs_render_fwd. */
+ * T_final / n_contrib of the matching unigs_render_fwd.  Each call first
+ * zeroes the per-(camera, Gaussian) gradient records it accumulates into
+ * (the pairs with a kept tile), so several backward passes may follow one
+ * forward. */
 unigs_status unigs_render_bwd(const unigs_plan* plan, const unigs_gaussians* g,
                               const unigs_camera* cams, void* ws, const unigs_outputs* fwd,
                               const unigs_grad_outputs* grad_out, unigs_param_grads* grads,

@@ -222,6 +222,9 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     sizes[OFF_SEM32] = sem32_needed(*plan) ? sizeof(float) * (size_t)g->n * g->n_sem : 0;
     sizes[OFF_ORDER] = sizeof(uint32_t) * (size_t)tiles;
     sizes[OFF_LOSS] = sizeof(float) * 8 * (size_t)LOSS_MAX_BLOCKS;
+    // per (camera, Gaussian): the short-axis row of the projected scaled axes
+    // E^T J R_wc R S, from the preprocess's double-float chain (float4)
+    sizes[OFF_VP] = sizeof(float) * 4 * (size_t)total;
     size_t off = 0;
     for (int r = 0; r < OFF_END; ++r) {
         plan->off[r] = off;
@@ -349,7 +352,7 @@ int32_t unigs_launches_per_step(const unigs_plan* plan) {
     }
     const int check = (plan->cfg.flags & UNIGS_FLAG_CHECK_FINITE) && plan->n > 0 ? 1 : 0;
     return 2 /*preprocess*/ + check + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ +
-           2 /*bwd*/;
+           3 /*bwd: record zeroing, composite, preprocess bwd*/;
 }
 
 int32_t unigs_plan_paths(const unigs_plan* plan) {

@@ -1,9 +1,9 @@
 // Double-float EWA projection of one Gaussian (Sec. 3.1 follows 3DGS's EWA
 // splatting): camera-frame centre, Jacobian terms and the projected scaled
-// axes V = J R_wc R S, the 2x3 factor of the 2D covariance V V^T.  Shared by
-// the preprocess (conic and centre of ill-conditioned splats) and the
-// preprocess backward (the projected axes of those splats in the frame the
-// covariance gradient is recorded in).
+// axes V = J R_wc R S, the 2x3 factor of the 2D covariance V V^T, from which
+// the preprocess derives the centre, the conic (and its conditional form),
+// the principal axes and, for the preprocess backward, the short-axis row of
+// V in that frame.
 #pragma once
 
 #include "ff.cuh"

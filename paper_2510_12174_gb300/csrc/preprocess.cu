@@ -142,6 +142,7 @@ struct SplatFF {
     float cxx, cyy;  // diagonal of the 2D covariance
     float ec, es;    // principal axis e0 = (ec, es) of the 2D covariance
     float lam0, lam1;  // its eigenvalues along e0 (the larger) and e1
+    float vp1[3];      // e1^T V: the short-axis row of the projected scaled axes
     // conditional form of the quadratic, q = P (a + rho b)^2 + e b^2 with the
     // pivot coordinate a = x when c11 > c00 (piv_x), else a = y
     float P, e;
@@ -176,6 +177,12 @@ __device__ __forceinline__ void splat_ff(const DevCam& cam, float mux, float muy
     // orthonormal pair is a valid frame; this one keeps the recorded
     // covariance gradient free of cancellation for thin splats)
     sincosf(0.5f * atan2f(2.f * ff_val(c01), ff_val(ff_sub(c00, c11))), &o.es, &o.ec);
+    // e1^T V in double-float, rounded: the preprocess backward's projected
+    // scaled axes along the short axis, orders of magnitude below V's entries
+    // for a thin splat seen far off-axis
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        o.vp1[j] = ff_val(ff_add(ff_mul_f(V[0][j], -o.es), ff_mul_f(V[1][j], o.ec)));
     {
         const float hd = 0.5f * ff_val(ff_sub(c00, c11)), co = ff_val(c01);
         o.lam0 = 0.5f * (ff_val(c00) + ff_val(c11)) + sqrtf(hd * hd + co * co);
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(256)
                       int tw, int th, float lowpass, float* __restrict__ rec,
                       uint2* __restrict__ rect,
                       uint32_t* __restrict__ touched, uint32_t* __restrict__ zbits,
-                      float* __restrict__ cull) {
+                      float* __restrict__ cull, float4* __restrict__ vp) {
     const int64_t n = g.n;
     const int64_t total = n * (int64_t)n_cams;
     const int lane = threadIdx.x & 31;
@@ -406,6 +413,7 @@ __global__ void __launch_bounds__(256)
             o[R_E0] = sqrtf(ql * sf.lam0) * 1.01f + 1.f;
             o[R_E1] = sqrtf(ql * fmaxf(sf.lam1, 0.f)) * 1.01f + 1.f;
         }
+        vp[t] = make_float4(sf.vp1[0], sf.vp1[1], sf.vp1[2], 0.f);
         float4* dst = reinterpret_cast<float4*>(rec + (size_t)t * REC_FLOATS);
 #pragma unroll
         for (int q = 0; q < REC_FLOATS / 4; ++q)
@@ -498,7 +506,7 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
             p.cfg.lowpass,
             ws_ptr<float>(ws, p, OFF_REC), ws_ptr<uint2>(ws, p, OFF_RECT),
             ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
-            ws_ptr<float>(ws, p, OFF_CULL));
+            ws_ptr<float>(ws, p, OFF_CULL), ws_ptr<float4>(ws, p, OFF_VP));
         ++launches;
     }
     if (sem32_needed(p)) {

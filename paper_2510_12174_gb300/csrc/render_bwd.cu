@@ -29,7 +29,6 @@
 #include "launch.h"
 #include "sh.cuh"
 #include "bwd_pair.cuh"
-#include "ewa_ff.cuh"
 
 namespace unigs {
 
@@ -365,6 +364,36 @@ __global__ void __launch_bounds__(256, (B <= 8 ? 3 : 2)) render_bwd_kernel(const
     if (timed_out && lane == 0) set_status(P.hdr, UNIGS_ERR_TIMEOUT);
 }
 
+// ------------------------------------------------------ record zeroing
+// Zeroes the gradient record (GREC_FLOATS doubles) of every (camera,
+// Gaussian) pair with a kept tile.  A warp reads 32 consecutive touched
+// counts, then clears the flagged records two at a time, one 16-byte store
+// per lane, so that each store instruction covers two whole records.
+__global__ void __launch_bounds__(256)
+    grec_zero_kernel(const uint32_t* __restrict__ touched, double2* __restrict__ grec,
+                     int64_t total) {
+    constexpr int PER = GREC_FLOATS / 2;  // 16-byte chunks per record
+    static_assert(PER == 16, "two records per warp-wide store");
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31;
+         base < total; base += stride) {
+        const int64_t t = base + lane;
+        uint32_t mask = __ballot_sync(0xffffffffu, t < total && touched[t] != 0);
+        while (mask) {
+            const int r0 = __ffs(mask) - 1;
+            mask &= mask - 1;
+            int r1 = -1;
+            if (mask) {
+                r1 = __ffs(mask) - 1;
+                mask &= mask - 1;
+            }
+            const int r = lane < PER ? r0 : r1;
+            if (r >= 0) grec[(base + r) * PER + (lane & (PER - 1))] = make_double2(0.0, 0.0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- kernel 2
 struct PreBwdParams {
     const CamTable* tab;
@@ -372,6 +401,7 @@ struct PreBwdParams {
     unigs_gaussians g;
     const float* rec;
     const double* grec;
+    const float4* vp;          // e1^T V per (camera, Gaussian), from the preprocess
     const uint32_t* touched;
     unigs_param_grads out;
     float lowpass;
@@ -477,24 +507,21 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
             // T^T G T has entries orders of magnitude above the gradients.
             const float* rp = P.rec + t * REC_FLOATS;
             const float ec = rp[R_EC], es = rp[R_ES];
+            // the long-axis row in float32 here; the short-axis row, orders of
+            // magnitude below T M's entries for a thin splat seen far
+            // off-axis, from the preprocess's double-float chain
             float Vp[2][3];
-            if (rp[R_FLAG] != 0.f) {
-                // ill-conditioned splat: V' in double-float (its short-axis
-                // row is orders of magnitude below T M's entries)
-                EwaFF e;
-                ewa_ff(cam, mu[0], mu[1], mu[2], q0[0], q0[1], q0[2], q0[3], s[0], s[1], s[2], e);
-                for (int j = 0; j < 3; ++j) {
-                    Vp[0][j] = ff_val(ff_add(ff_mul_f(e.V[0][j], ec), ff_mul_f(e.V[1][j], es)));
-                    Vp[1][j] = ff_val(ff_add(ff_mul_f(e.V[0][j], -es), ff_mul_f(e.V[1][j], ec)));
-                }
-            } else {
-                for (int j = 0; j < 3; ++j) {
-                    float tm[2];
-                    for (int a = 0; a < 2; ++a)
-                        tm[a] = Tm[a][0] * M[0][j] + Tm[a][1] * M[1][j] + Tm[a][2] * M[2][j];
-                    Vp[0][j] = ec * tm[0] + es * tm[1];
-                    Vp[1][j] = -es * tm[0] + ec * tm[1];
-                }
+            {
+                const float4 v1 = P.vp[t];
+                Vp[1][0] = v1.x;
+                Vp[1][1] = v1.y;
+                Vp[1][2] = v1.z;
+            }
+            for (int j = 0; j < 3; ++j) {
+                float tm[2];
+                for (int a = 0; a < 2; ++a)
+                    tm[a] = Tm[a][0] * M[0][j] + Tm[a][1] * M[1][j] + Tm[a][2] * M[2][j];
+                Vp[0][j] = ec * tm[0] + es * tm[1];
             }
             const float Gp[2][2] = {{gr[G_CA], 0.5f * gr[G_CB]}, {0.5f * gr[G_CB], gr[G_CC]}};
             float GV[2][3];
@@ -631,7 +658,16 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
                       const unigs_param_grads& grads, cudaStream_t st) {
     int launches = 0;
     double* grec = ws_ptr<double>(ws, p, OFF_GREC);
-    cudaMemsetAsync(grec, 0, sizeof(double) * GREC_FLOATS * (size_t)p.n * p.n_cams, st);
+    if (p.n > 0) {
+        // zero the records the composite may accumulate into: those of the
+        // (camera, Gaussian) pairs with a kept tile
+        const int64_t total = p.n * (int64_t)p.n_cams;
+        const int64_t blocks = (total + 255) / 256;
+        const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+        grec_zero_kernel<<<grid, 256, 0, st>>>(ws_ptr<uint32_t>(ws, p, OFF_TOUCH),
+                                               reinterpret_cast<double2*>(grec), total);
+        ++launches;
+    }
     if (grads.sem && !grads.accumulate && p.n_sem > 0)
         cudaMemsetAsync(grads.sem, 0, sizeof(float) * (size_t)p.n * p.n_sem, st);
     if (p.n_tiles > 0 && p.n > 0 && bwd_tc_selected(p)) {
@@ -684,6 +720,7 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         Q.g = g;
         Q.rec = ws_ptr<float>(ws, p, OFF_REC);
         Q.grec = grec;
+        Q.vp = ws_ptr<float4>(ws, p, OFF_VP);
         Q.touched = ws_ptr<uint32_t>(ws, p, OFF_TOUCH);
         Q.out = grads;
         Q.lowpass = p.cfg.lowpass;

@@ -150,8 +150,9 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 enum {
     OFF_HDR = 0, OFF_CAM, OFF_REC, OFF_RECT, OFF_TOUCH, OFF_OFFS, OFF_ZBITS,
     OFF_SCAN, OFF_KEYS0, OFF_KEYS1, OFF_VALS0, OFF_VALS1, OFF_HIST, OFF_RANGES,
-    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_ORDER, OFF_LOSS, OFF_END
+    OFF_GREC, OFF_CULL, OFF_SEM32, OFF_ORDER, OFF_LOSS, OFF_VP, OFF_END
 };
+static_assert(OFF_END <= 20, "unigs_plan::off holds 20 region offsets");
 
 // Per-(camera, Gaussian) record of the opacity-aware tile test (8 floats):
 // float32 projected centre, float32 conic (kA, kB, kC), qlim, no-cull flag.
