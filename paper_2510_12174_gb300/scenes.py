@@ -386,3 +386,40 @@ def synthetic_targets(cams: Sequence[Camera], n_sem: int, seed: int) -> dict:
         lab[rng.uniform(size=(H, W)) < 0.1] = -1
         out["label"].append(lab.astype(np.int32))
     return out
+
+
+def anchor_set(n: int = 1000, n_offsets: int = 10, n_sem: int = 24, seed: int = 11,
+               feat_dim: int = 32, hidden: int = 32, opacity_bias: float = 1.0):
+    """Seeded synthetic anchor set and MLP parameters (row-per-anchor arrays,
+    float32): anchors in a box in front of the identity camera of
+    ``small_room`` (x in [-1.5, 1.5], y in [-1, 1], z in [2, 5]), log-normal
+    scales around 0.07, offsets N(0, 1) in units of the scale, features and
+    base logits N(0, 1), base k in [0.8, 1.2]; MLP weights N(0, 1/F) and
+    N(0, 2/H) (unit-variance pre-activations), biases N(0, 0.1), the opacity
+    branch's output bias shifted by ``opacity_bias``.  Returns (arrays, mlps)
+    with mlps[name] = {w1 [H,F], b1 [H], w2 [out,H], b2 [out]}."""
+    rng = np.random.default_rng(seed)
+    f32 = np.float32
+    lo, hi = np.array([-1.5, -1.0, 2.0]), np.array([1.5, 1.0, 5.0])
+    arrs = {
+        "pos": rng.uniform(lo, hi, size=(n, 3)).astype(f32),
+        "scale": np.exp(rng.normal(-2.6, 0.3, size=(n, 3))).astype(f32),
+        "offsets": rng.normal(0.0, 1.0, size=(n, n_offsets, 3)).astype(f32),
+        "feat": rng.normal(0.0, 1.0, size=(n, feat_dim)).astype(f32),
+        "sem": rng.normal(0.0, 1.0, size=(n, n_sem)).astype(f32),
+        "kfac": rng.uniform(0.8, 1.2, size=n).astype(f32),
+    }
+    outs = {"sem": n_sem, "k": 1, "opacity": n_offsets, "color": 3 * n_offsets,
+            "cov": 7 * n_offsets}
+    mlps = {}
+    for name, out in outs.items():
+        if out == 0:
+            continue
+        mlps[name] = {
+            "w1": (rng.normal(0.0, 1.0, size=(hidden, feat_dim)) / np.sqrt(feat_dim)).astype(f32),
+            "b1": rng.normal(0.0, 0.1, size=hidden).astype(f32),
+            "w2": (rng.normal(0.0, 1.0, size=(out, hidden)) * np.sqrt(2.0 / hidden)).astype(f32),
+            "b2": (rng.normal(0.0, 0.1, size=out) + (opacity_bias if name == "opacity" else 0.0))
+            .astype(f32),
+        }
+    return arrs, mlps
