@@ -1,4 +1,5 @@
-"""ctypes binding of the libunigs C ABI (include/unigs.h, include/unigs_train.h).
+"""ctypes binding of the libunigs C ABI (include/unigs.h, include/unigs_train.h,
+include/unigs_anchors.h).
 
 Argument marshalling only: every function here forwards to the entry point
 of the same name; all arithmetic runs in the library's kernels.  Loading
@@ -114,6 +115,40 @@ class unigs_prune_array(Structure):
                 ("reserved", c_int32)]
 
 
+UNIGS_ANCHOR_FEAT = 32
+UNIGS_ANCHOR_HIDDEN = 32
+UNIGS_ANCHOR_MAX_OFFSETS = 16
+ANCHOR_MLPS = ("sem", "k", "opacity", "color", "cov")
+
+
+class unigs_mlp(Structure):
+    _fields_ = [("w1", c_void_p), ("b1", c_void_p), ("w2", c_void_p), ("b2", c_void_p)]
+
+
+class unigs_anchors(Structure):
+    _fields_ = [("n", c_int64), ("n_offsets", c_int32), ("feat_dim", c_int32),
+                ("hidden", c_int32), ("n_sem", c_int32), ("pos", c_void_p), ("scale", c_void_p),
+                ("offsets", c_void_p), ("feat", c_void_p), ("sem", c_void_p),
+                ("kfac", c_void_p)] + [("mlp_" + n, unigs_mlp) for n in ANCHOR_MLPS]
+
+
+class unigs_anchor_gaussians(Structure):
+    _fields_ = [("mean", c_void_p), ("quat", c_void_p), ("scale", c_void_p),
+                ("opacity", c_void_p), ("kfac", c_void_p), ("sh", c_void_p), ("sem", c_void_p),
+                ("feat_dtype", c_int32), ("reserved", c_int32)]
+
+
+class unigs_mlp_grads(Structure):
+    _fields_ = [("w1", c_void_p), ("b1", c_void_p), ("w2", c_void_p), ("b2", c_void_p)]
+
+
+class unigs_anchor_grads(Structure):
+    _fields_ = [("pos", c_void_p), ("scale", c_void_p), ("offsets", c_void_p),
+                ("feat", c_void_p), ("sem", c_void_p), ("kfac", c_void_p)] + \
+               [("mlp_" + n, unigs_mlp_grads) for n in ANCHOR_MLPS] + \
+               [("accumulate", c_int32), ("reserved", c_int32)]
+
+
 UNIGS_LOSS_TOTAL, UNIGS_LOSS_L1, UNIGS_LOSS_NORMAL, UNIGS_LOSS_DEPTH = 0, 1, 2, 3
 UNIGS_LOSS_SEG, UNIGS_LOSS_K = 4, 5
 UNIGS_LOSS_W_L1, UNIGS_LOSS_W_NORMAL, UNIGS_LOSS_W_DEPTH = 6, 7, 8
@@ -167,6 +202,11 @@ _SIGS = [
                                    c_void_p]),
     ("unigs_prune_compact", c_int32, [POINTER(unigs_prune_array), c_int32, c_int64, c_int64,
                                       c_void_p, c_void_p]),
+    # include/unigs_anchors.h
+    ("unigs_anchor_decode", c_int32, [POINTER(unigs_anchors), POINTER(unigs_anchor_gaussians),
+                                      c_void_p]),
+    ("unigs_anchor_decode_bwd", c_int32, [POINTER(unigs_anchors), POINTER(unigs_param_grads),
+                                          POINTER(unigs_anchor_grads), c_void_p]),
 ]
 
 
@@ -316,3 +356,12 @@ def unigs_prune_mark(k, n, T_k, ws, n_keep, stream) -> int:
 
 def unigs_prune_compact(arrays, n_arrays, n, n_keep, ws, stream) -> int:
     return lib().unigs_prune_compact(arrays, n_arrays, n, n_keep, ws, stream)
+
+
+def unigs_anchor_decode(a, out, stream) -> int:
+    return lib().unigs_anchor_decode(ctypes.byref(a), ctypes.byref(out), stream)
+
+
+def unigs_anchor_decode_bwd(a, g, out, stream) -> int:
+    return lib().unigs_anchor_decode_bwd(ctypes.byref(a), ctypes.byref(g), ctypes.byref(out),
+                                         stream)

@@ -1,6 +1,7 @@
 // C ABI of libunigs: plan, workspace layout, argument checks, entry points.
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -27,15 +28,18 @@ int sm_count() {
 
 cudaError_t ensure_smem_limit(const void* func, int bytes) {
     static std::mutex mu;
-    static std::set<std::pair<const void*, int>> done;  // (kernel, device)
+    // (kernel, device) -> the largest limit set so far (kernels whose
+    // shared memory depends on runtime sizes raise it when they need more)
+    static std::map<std::pair<const void*, int>, int> done;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
     const auto key = std::make_pair(func, dev);
-    if (done.count(key)) return cudaSuccess;
+    const auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done.insert(key);
+    if (e == cudaSuccess) done[key] = bytes;
     return e;
 }
 }  // namespace unigs

@@ -115,10 +115,10 @@ def grad_errors(got, ref):
     return res
 
 
-def check_grad_errors(e, tol=1e-3, norm=1e-4):
+def check_grad_errors(e, tol=1e-3, norm=1e-4, strict_fraction=STRICT_FRACTION):
     """Gradient criterion, every element of every parameter type:
     |g - g_ref| <= tol * max(|g_ref|, GRAD_FLOOR * RMS); at most a fraction
-    STRICT_FRACTION of the elements above tol * max(|g_ref|, STRICT_FLOOR *
+    ``strict_fraction`` of the elements above tol * max(|g_ref|, STRICT_FLOOR *
     RMS); and the whole vector within ``norm`` relative error."""
     for k, d in e.items():
         print(f"grad {k}: max {d['max']:.2e} (floor {GRAD_FLOOR:g} rms) max {d['max_strict']:.2e} "
@@ -126,7 +126,7 @@ def check_grad_errors(e, tol=1e-3, norm=1e-4):
               f"rms {d['rms']:.3e}")
     for k, d in e.items():
         assert d["max"] < tol, (k, d)
-        assert d["frac_strict"] <= STRICT_FRACTION, (k, d)
+        assert d["frac_strict"] <= strict_fraction, (k, d)
         assert d["norm"] < norm, (k, d)
 
 
