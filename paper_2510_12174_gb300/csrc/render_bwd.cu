@@ -407,7 +407,13 @@ struct PreBwdParams {
     float lowpass;
 };
 
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams P) {
+// DEG is the SH degree: with the basis size a compile-time constant the
+// basis, its gradient and the coefficient gradients are registers, not
+// local memory.  Three 128-thread blocks per SM (a few spilled registers at
+// degree 3) hide more load latency than two without spills.
+template <int DEG>
+__global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(const PreBwdParams P) {
+    constexpr int n_sh = (DEG + 1) * (DEG + 1);
     const int64_t n = P.g.n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -436,10 +442,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
         float g_mu[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {}, g_s[3] = {0.f, 0.f, 0.f};
         float g_th[3] = {0.f, 0.f, 0.f};  // rotation R -> R exp([theta]_x)
         float g_op = 0.f, g_k = 0.f;
-        const int deg = P.g.sh_degree;
-        const int n_sh = (deg + 1) * (deg + 1);
-        float g_sh[16][3];
-        for (int k = 0; k < 16; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+        float g_sh[n_sh][3];
+#pragma unroll
+        for (int k = 0; k < n_sh; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
 
         for (int k = 0; k < P.n_cams; ++k) {
             const size_t t = (size_t)k * (size_t)n + (size_t)i;
@@ -463,20 +468,26 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
                 const float il = 1.f / len;
                 d[0] *= il; d[1] *= il; d[2] *= il;
                 float Y[16];
-                sh_eval_basis(d[0], d[1], d[2], deg, Y);
+                sh_eval_basis(d[0], d[1], d[2], DEG, Y);
                 float dY[16][3];
-                sh_eval_basis_grad(d[0], d[1], d[2], deg, dY);
+                sh_eval_basis_grad(d[0], d[1], d[2], DEG, dY);
                 float g_dir[3] = {0.f, 0.f, 0.f};
                 const size_t shb = (size_t)i * n_sh * 3;
+#pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
+                    float hc[n_sh];
                     float raw = 0.5f;
-                    for (int kk = 0; kk < n_sh; ++kk)
-                        raw = fmaf(Y[kk], load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype), raw);
+#pragma unroll
+                    for (int kk = 0; kk < n_sh; ++kk) {
+                        hc[kk] = load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype);
+                        raw = fmaf(Y[kk], hc[kk], raw);
+                    }
                     if (raw < 0.f) continue;  // clamped at 0
                     const float gc = gr[G_RGB + ch];
+#pragma unroll
                     for (int kk = 0; kk < n_sh; ++kk) {
                         g_sh[kk][ch] = fmaf(Y[kk], gc, g_sh[kk][ch]);
-                        const float h = load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype) * gc;
+                        const float h = hc[kk] * gc;
                         g_dir[0] = fmaf(h, dY[kk][0], g_dir[0]);
                         g_dir[1] = fmaf(h, dY[kk][1], g_dir[1]);
                         g_dir[2] = fmaf(h, dY[kk][2], g_dir[2]);
@@ -624,7 +635,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(const PreBwdParams 
         for (int a = 0; a < 4; ++a) PUT(O.quat, a * n + i, g_q[a]);
         PUT(O.opacity, i, g_op);
         PUT(O.kfac, i, g_k);
+#pragma unroll
         for (int kk = 0; kk < n_sh; ++kk)
+#pragma unroll
             for (int ch = 0; ch < 3; ++ch) PUT(O.sh, ((size_t)i * n_sh + kk) * 3 + ch, g_sh[kk][ch]);
 #undef PUT
     }
@@ -663,7 +676,8 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         // (camera, Gaussian) pairs with a kept tile
         const int64_t total = p.n * (int64_t)p.n_cams;
         const int64_t blocks = (total + 255) / 256;
-        const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+        const int64_t cap = (int64_t)sm_count() * 16;
+        const int grid = (int)(blocks < cap ? blocks : cap);
         grec_zero_kernel<<<grid, 256, 0, st>>>(ws_ptr<uint32_t>(ws, p, OFF_TOUCH),
                                                reinterpret_cast<double2*>(grec), total);
         ++launches;
@@ -725,8 +739,14 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         Q.out = grads;
         Q.lowpass = p.cfg.lowpass;
         const int64_t blocks = (p.n + 127) / 128;
-        const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-        preprocess_bwd_kernel<<<grid, 128, 0, st>>>(Q);
+        const int64_t cap = (int64_t)sm_count() * 32;
+        const int grid = (int)(blocks < cap ? blocks : cap);
+        switch (g.sh_degree) {
+            case 0: preprocess_bwd_kernel<0><<<grid, 128, 0, st>>>(Q); break;
+            case 1: preprocess_bwd_kernel<1><<<grid, 128, 0, st>>>(Q); break;
+            case 2: preprocess_bwd_kernel<2><<<grid, 128, 0, st>>>(Q); break;
+            default: preprocess_bwd_kernel<3><<<grid, 128, 0, st>>>(Q); break;
+        }
         ++launches;
     }
     return launches;

@@ -211,6 +211,20 @@ def test_backward_parity_bf16_features():
     check_grad_errors(_grad_case(sc, cams), norm=3e-4)
 
 
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_sh_degrees_forward_and_backward(deg):
+    """The preprocess and its backward compile one path per SH degree: the
+    colours and every gradient (the SH coefficients' included) against the
+    oracle at degrees 0-2 (degree 3 is every other test's)."""
+    sc, cams = scenes.small_room(n=5000, width=64, height=52, n_sem=8, seed=40 + deg,
+                                 sh_degree=deg, n_cams=2)
+    r, out = _render(sc, cams)
+    _, ref, _ = oracle.render(sc, cams, with_normal_d=False)
+    e = forward_errors(r, out, ref, sc.n_sem)
+    assert e["rgb"] < TOL_ABS and e["depth"] < TOL_REL, e
+    check_grad_errors(_grad_case(sc, cams, seed=50 + deg))
+
+
 def test_center_depth_ablation_forward_and_backward():
     """UNIGS_FLAG_CENTER_DEPTH (the centre-depth ablation of Tab. 6) against
     the oracle in the same mode: forward depth and the gradients."""
