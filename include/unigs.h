@@ -15,7 +15,9 @@
  * ---------------------------------------
  * - Every pointer argument marked "device" is caller-owned device memory.
  *   The library never allocates or frees memory and keeps no global mutable
- *   state; the caller allocates one workspace of unigs_workspace_bytes().
+ *   state beyond host-side caches of device attributes (the SM count, and the
+ *   shared-memory limit set per kernel and device, under a mutex); the caller
+ *   allocates one workspace of unigs_workspace_bytes().
  *   The one exception is unigs_sort_pairs_static (end of this header): its
  *   scratch is a static device array of the library, shared by every call,
  *   with a process-wide cache of that array's address per device.

@@ -2,6 +2,7 @@
 #include <string.h>
 
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -14,16 +15,17 @@ using namespace unigs;
 
 namespace unigs {
 int sm_count() {
-    static int cached[64] = {};
+    // per device; concurrent first calls store the same value
+    static std::atomic<int> cached[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (!cached[dev]) {
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 152;
-        cached[dev] = n;
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (!c) {
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0)
+            c = 152;
+        cached[dev].store(c, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return c;
 }
 
 cudaError_t ensure_smem_limit(const void* func, int bytes) {

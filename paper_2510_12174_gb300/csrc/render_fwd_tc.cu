@@ -409,12 +409,8 @@ __global__ void __launch_bounds__(256, (B <= 16 ? 4 : 2)) render_fwd_tc_kernel(c
 template <int NS, int B, bool F32>
 static void launch_fwd_tc_t(const FwdTcParams& P, int grid, cudaStream_t st) {
     const size_t smem = sizeof(FwdTcSmem<NS, B, F32>);
-    static bool attr_set = false;  // host-side, set once per instantiation
-    if (!attr_set) {
-        cudaFuncSetAttribute(render_fwd_tc_kernel<NS, B, F32>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    // per device; a failure surfaces as the launch error the entry point returns
+    ensure_smem_limit(reinterpret_cast<const void*>(&render_fwd_tc_kernel<NS, B, F32>), (int)smem);
     render_fwd_tc_kernel<NS, B, F32><<<grid, 256, smem, st>>>(P);
 }
 
