@@ -54,9 +54,8 @@ struct DecodeOut {
 
 __device__ __forceinline__ float sigm(float y) { return 1.f / (1.f + expf(-y)); }
 
-template <bool BF16>
-__device__ __forceinline__ void put_feat(void* base, int64_t i, float v) {
-    if (BF16)
+__device__ __forceinline__ void put_feat(void* base, int64_t i, float v, bool bf16) {
+    if (bf16)
         static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(v);
     else
         static_cast<float*>(base)[i] = v;
@@ -114,52 +113,57 @@ __device__ __forceinline__ void load_feat(const AnchorIn& P, int64_t a, float (&
     }
 }
 
-template <bool BF16>
+// The five branches run in a loop that is not unrolled, so the kernel holds
+// one copy of the fully unrolled 32 x 32 hidden layer (five copies made the
+// translation unit take minutes to compile).
 __global__ void __launch_bounds__(ATHREADS) anchor_decode_kernel(const AnchorIn P, const WLayout L,
-                                                                 const DecodeOut O) {
+                                                                 const DecodeOut O, int bf16) {
     extern __shared__ __align__(16) float sw[];
     load_weights(P, L, sw);
     __syncthreads();
     const int M = P.M, C = P.C;
     const int64_t N = P.n * M;
+    const bool fb = bf16 != 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < P.n;
          a += (int64_t)gridDim.x * blockDim.x) {
         float f[AF], h[AH];
         uint32_t mask;
         load_feat(P, a, f);
         const int64_t g0 = a * M;
-        // semantic logits: o_ah (x) sigma(MLP_sem(f)), the same for every child
-        if (C > 0) {
-            hidden_layer(sw, L, 0, f, h, &mask);
-            for (int c = 0; c < C; ++c) {
-                const float o = P.sem[a * C + c] * sigm(mlp_out(sw, L, 0, h, c));
-                for (int m = 0; m < M; ++m) put_feat<BF16>(O.sem, (g0 + m) * C + c, o);
-            }
-        }
-        // gradient factor: k_ah sigma(MLP_k(f))
-        hidden_layer(sw, L, 1, f, h, &mask);
-        {
-            const float k = P.kfac[a] * sigm(mlp_out(sw, L, 1, h, 0));
-            for (int m = 0; m < M; ++m) O.kfac[g0 + m] = k;
-        }
-        // opacity
-        hidden_layer(sw, L, 2, f, h, &mask);
-        for (int m = 0; m < M; ++m) O.opacity[g0 + m] = sigm(mlp_out(sw, L, 2, h, m));
-        // colour as the degree-0 SH coefficient
-        hidden_layer(sw, L, 3, f, h, &mask);
-        for (int m = 0; m < M; ++m)
-            for (int ch = 0; ch < 3; ++ch) {
-                const float c = sigm(mlp_out(sw, L, 3, h, 3 * m + ch));
-                put_feat<BF16>(O.sh, (g0 + m) * 3 + ch, (c - 0.5f) / Y00);
-            }
-        // scale and rotation
-        hidden_layer(sw, L, 4, f, h, &mask);
         const float l[3] = {P.scale[a], P.scale[P.n + a], P.scale[2 * P.n + a]};
-        for (int m = 0; m < M; ++m) {
-            const int64_t g = g0 + m;
-            for (int i = 0; i < 3; ++i)
-                O.scale[i * N + g] = l[i] * sigm(mlp_out(sw, L, 4, h, 7 * m + i));
-            for (int j = 0; j < 4; ++j) O.quat[j * N + g] = mlp_out(sw, L, 4, h, 7 * m + 3 + j);
+#pragma unroll 1
+        for (int X = 0; X < NMLP; ++X) {
+            if (L.out[X] == 0) continue;  // no semantic branch without logits
+            hidden_layer(sw, L, X, f, h, &mask);
+            if (X == 0) {
+                // semantic logits: o_ah (x) sigma(MLP_sem(f)), the same for every child
+                for (int c = 0; c < C; ++c) {
+                    const float o = P.sem[a * C + c] * sigm(mlp_out(sw, L, 0, h, c));
+                    for (int m = 0; m < M; ++m) put_feat(O.sem, (g0 + m) * C + c, o, fb);
+                }
+            } else if (X == 1) {
+                // gradient factor: k_ah sigma(MLP_k(f))
+                const float k = P.kfac[a] * sigm(mlp_out(sw, L, 1, h, 0));
+                for (int m = 0; m < M; ++m) O.kfac[g0 + m] = k;
+            } else if (X == 2) {
+                for (int m = 0; m < M; ++m) O.opacity[g0 + m] = sigm(mlp_out(sw, L, 2, h, m));
+            } else if (X == 3) {
+                // colour as the degree-0 SH coefficient
+                for (int m = 0; m < M; ++m)
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const float c = sigm(mlp_out(sw, L, 3, h, 3 * m + ch));
+                        put_feat(O.sh, (g0 + m) * 3 + ch, (c - 0.5f) / Y00, fb);
+                    }
+            } else {
+                // scale and rotation
+                for (int m = 0; m < M; ++m) {
+                    const int64_t g = g0 + m;
+                    for (int i = 0; i < 3; ++i)
+                        O.scale[i * N + g] = l[i] * sigm(mlp_out(sw, L, 4, h, 7 * m + i));
+                    for (int j = 0; j < 4; ++j)
+                        O.quat[j * N + g] = mlp_out(sw, L, 4, h, 7 * m + 3 + j);
+                }
+            }
         }
         // position: x + l (x) O_m
         const float x[3] = {P.pos[a], P.pos[P.n + a], P.pos[2 * P.n + a]};
@@ -450,15 +454,8 @@ extern "C" unigs_status unigs_anchor_decode(const unigs_anchors* a,
     const size_t smem = sizeof(float) * (size_t)L.total;
     const int grid = anchor_grid(a->n);
     cudaStream_t st = (cudaStream_t)stream;
-    if (out->feat_dtype) {
-        unigs::ensure_smem_limit(reinterpret_cast<const void*>(&unigs::anchor_decode_kernel<true>),
-                                 (int)smem);
-        unigs::anchor_decode_kernel<true><<<grid, unigs::ATHREADS, smem, st>>>(P, L, O);
-    } else {
-        unigs::ensure_smem_limit(reinterpret_cast<const void*>(&unigs::anchor_decode_kernel<false>),
-                                 (int)smem);
-        unigs::anchor_decode_kernel<false><<<grid, unigs::ATHREADS, smem, st>>>(P, L, O);
-    }
+    unigs::ensure_smem_limit(reinterpret_cast<const void*>(&unigs::anchor_decode_kernel), (int)smem);
+    unigs::anchor_decode_kernel<<<grid, unigs::ATHREADS, smem, st>>>(P, L, O, out->feat_dtype);
     return launch_status();
 }
 
