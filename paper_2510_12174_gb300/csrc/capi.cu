@@ -196,6 +196,9 @@ unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g, const u
     plan->n_tiles = tiles;
     plan->n_pixels = pixels;
     const int64_t total = g->n * (int64_t)n_cams;
+    // a (camera, Gaussian) pair index is 32 bits wide in the device lists (the
+    // per-pair workspace, over 500 bytes a pair, bounds it far lower anyway)
+    if (total >= ((int64_t)1 << 32)) return UNIGS_ERR_INVALID_ARG;
     int64_t cap = instance_capacity ? instance_capacity : 4 * total;
     if (cap > 0x7fffffffLL) cap = 0x7fffffffLL;
     plan->capacity = cap;
@@ -357,7 +360,7 @@ int32_t unigs_launches_per_step(const unigs_plan* plan) {
         conv = (cnt / 2 > 0 ? 1 : 0) + (int)(cnt & 1);
     }
     const int check = (plan->cfg.flags & UNIGS_FLAG_CHECK_FINITE) && plan->n > 0 ? 1 : 0;
-    return 2 /*preprocess*/ + check + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ +
+    return 3 /*preprocess: init, culling pass, splat pass*/ + check + conv + bin + 1 /*fwd*/ + 1 /*dn fwd*/ + 1 /*dn bwd*/ +
            3 /*bwd: record zeroing, composite, preprocess bwd*/;
 }
 

@@ -1,4 +1,8 @@
-// Preprocess: one thread per (camera, Gaussian).
+// Preprocess, in two kernels.  The culling pass takes one thread per (camera,
+// Gaussian): the binning recipe, the opacity-aware tile count and the list of
+// pairs with a kept tile.  The splat pass takes one thread per listed pair:
+// the continuous setup below and the record.  Culled pairs would otherwise
+// leave most lanes of a warp idle through the long double-float chain.
 //
 // Discrete part (projected centre, EWA 2D covariance with the 0.3 px
 // low-pass, 3-sigma radius, tile rectangle, depth key) follows a fixed
@@ -241,10 +245,10 @@ __device__ __forceinline__ uint32_t count_kept_serial(const float* cr, int x0, i
 
 __global__ void __launch_bounds__(256)
     preprocess_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab, int n_cams,
-                      int tw, int th, float lowpass, float* __restrict__ rec,
-                      uint2* __restrict__ rect,
+                      int tw, int th, float lowpass, uint2* __restrict__ rect,
                       uint32_t* __restrict__ touched, uint32_t* __restrict__ zbits,
-                      float* __restrict__ cull, float4* __restrict__ vp) {
+                      float* __restrict__ cull, WsHeader* __restrict__ hdr,
+                      uint32_t* __restrict__ kept_list) {
     const int64_t n = g.n;
     const int64_t total = n * (int64_t)n_cams;
     const int lane = threadIdx.x & 31;
@@ -294,6 +298,16 @@ __global__ void __launch_bounds__(256)
             }
             if (lane == src) kept = cnt;
         }
+        // the pairs with a kept tile go to the splat setup, appended warp by
+        // warp (one atomic per warp) so that its warps run full
+        const bool push = act && rc.valid && kept != 0;
+        const unsigned pm = __ballot_sync(0xffffffffu, push);
+        if (pm) {
+            uint32_t slot = 0;
+            if (lane == 0) slot = atomicAdd(&hdr->n_kept, (uint32_t)__popc(pm));
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (push) kept_list[slot + __popc(pm & ((1u << lane) - 1u))] = (uint32_t)t;
+        }
         if (!act) continue;
         if (!rc.valid) {
             touched[t] = 0;
@@ -308,7 +322,35 @@ __global__ void __launch_bounds__(256)
         float4* cdst = reinterpret_cast<float4*>(cull + (size_t)t * CULL_FLOATS);
         cdst[0] = make_float4(cr[0], cr[1], cr[2], cr[3]);
         cdst[1] = make_float4(cr[4], cr[5], cr[6], cr[7]);
-        if (kept == 0) continue;
+    }
+}
+
+// Splat setup of the pairs with a kept tile (the list the culling pass
+// appended): the double-float conic and centre, the principal axes, the SH
+// colour and the ray-ellipsoid record.  The binning recipe is recomputed (the
+// same bits as in the culling pass) for the rotation, depth and radius.
+__global__ void __launch_bounds__(256)
+    preprocess_splat_kernel(const unigs_gaussians g, const CamTable* __restrict__ tab,
+                            float lowpass, const uint32_t* __restrict__ kept_list,
+                            const WsHeader* __restrict__ hdr, const float* __restrict__ cull,
+                            float* __restrict__ rec, float4* __restrict__ vp) {
+    const int64_t n = g.n;
+    const uint32_t n_kept = hdr->n_kept;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_kept;
+         idx += gridDim.x * blockDim.x) {
+        const int64_t t = kept_list[idx];
+        const int k = (int)(t / n);
+        const int64_t i = t - (int64_t)k * n;
+        const DevCam& cam = tab->cam[k];
+        const float mux = __ldg(g.mean + i), muy = __ldg(g.mean + n + i),
+                    muz = __ldg(g.mean + 2 * n + i);
+        const float qw = __ldg(g.quat + i), qx = __ldg(g.quat + n + i),
+                    qy = __ldg(g.quat + 2 * n + i), qz = __ldg(g.quat + 3 * n + i);
+        const float sx = __ldg(g.scale + i), sy = __ldg(g.scale + n + i),
+                    sz = __ldg(g.scale + 2 * n + i);
+        Recipe rc;
+        binning_recipe(cam, mux, muy, muz, qw, qx, qy, qz, sx, sy, sz, lowpass, rc);
+        const float qlim = cull[(size_t)t * CULL_FLOATS + C_QLIM];
 
         float o[REC_FLOATS];
         SplatFF sf;
@@ -405,7 +447,7 @@ __global__ void __launch_bounds__(256)
             // box of the q <= qlim ellipse (x half-extent sqrt(qlim * Sigma_xx)),
             // with a relative and a one-pixel margin, clipped to the 3-sigma
             // square (plus a margin far above the float32 error of the centre)
-            const float ql = fmaxf(cr[C_QLIM], 0.f);
+            const float ql = fmaxf(qlim, 0.f);
             const float sq = rc.radius + 0.01f;
             o[R_EXTX] = fminf(sqrtf(ql * sf.cxx) * 1.01f + 1.f, sq);
             o[R_EXTY] = fminf(sqrtf(ql * sf.cyy) * 1.01f + 1.f, sq);
@@ -432,6 +474,7 @@ __global__ void init_kernel(CamTable tab, int n_cams, CamTable* __restrict__ dst
         hdr->n_eval = 0;
         hdr->n_blend = 0;
         hdr->nonfinite = 0;
+        hdr->n_kept = 0;
     }
 }
 
@@ -499,15 +542,26 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
         ++launches;
     }
     if (total > 0) {
+        // the list of pairs with a kept tile lives in the scan-offset region,
+        // which the binning overwrites afterwards (plan_init bounds the pair
+        // count below 2^32, so a pair index fits 32 bits)
+        uint32_t* kept_list = ws_ptr<uint32_t>(ws, p, OFF_OFFS);
+        WsHeader* hdr = ws_ptr<WsHeader>(ws, p, OFF_HDR);
         const int64_t blocks = (total + 255) / 256;
-        const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
+        const int64_t cap = (int64_t)sm_count() * 64;
+        const int grid = (int)(blocks < cap ? blocks : cap);
         preprocess_kernel<<<grid, 256, 0, st>>>(
             g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.n_cams, p.cfg.tile_w, p.cfg.tile_h,
-            p.cfg.lowpass,
-            ws_ptr<float>(ws, p, OFF_REC), ws_ptr<uint2>(ws, p, OFF_RECT),
-            ws_ptr<uint32_t>(ws, p, OFF_TOUCH), ws_ptr<uint32_t>(ws, p, OFF_ZBITS),
-            ws_ptr<float>(ws, p, OFF_CULL), ws_ptr<float4>(ws, p, OFF_VP));
-        ++launches;
+            p.cfg.lowpass, ws_ptr<uint2>(ws, p, OFF_RECT), ws_ptr<uint32_t>(ws, p, OFF_TOUCH),
+            ws_ptr<uint32_t>(ws, p, OFF_ZBITS), ws_ptr<float>(ws, p, OFF_CULL), hdr, kept_list);
+        // grid-stride over the list, whose length only the device knows
+        const int64_t cap2 = (int64_t)sm_count() * 8;
+        const int grid2 = (int)(blocks < cap2 ? blocks : cap2);
+        preprocess_splat_kernel<<<grid2, 256, 0, st>>>(
+            g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.cfg.lowpass, kept_list, hdr,
+            ws_ptr<float>(ws, p, OFF_CULL), ws_ptr<float>(ws, p, OFF_REC),
+            ws_ptr<float4>(ws, p, OFF_VP));
+        launches += 2;
     }
     if (sem32_needed(p)) {
         // n * n_sem is even whenever n_sem is (rows of 2-element pairs); an odd

@@ -142,7 +142,8 @@ struct WsHeader {
     uint32_t work_fwd;           // tile counters of the persistent composite kernels
     uint32_t work_bwd;
     uint32_t nonfinite;          // first parameter array found non-finite (flag set)
-    uint32_t pad[53];
+    uint32_t n_kept;             // (camera, Gaussian) pairs with a kept tile (preprocess)
+    uint32_t pad[52];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader layout");
 
