@@ -237,7 +237,10 @@ __global__ void __launch_bounds__(256)
 // Stable scatter.  Warp w of the block owns keys [w*256, w*256+256) of the
 // block's chunk and walks them 32 at a time in order; __match_any_sync ranks
 // equal digits inside each step, a per-warp running count orders the steps,
-// and a prefix over warps orders the warps.
+// and a prefix over warps orders the warps.  The block's pairs are first
+// placed in shared memory in (digit, input order) order, then written out by
+// consecutive threads: the pairs of one digit land at consecutive addresses,
+// so the stores coalesce.
 __global__ void __launch_bounds__(256)
     radix_scatter_kernel(const unsigned long long* __restrict__ kin,
                          const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
@@ -245,12 +248,17 @@ __global__ void __launch_bounds__(256)
                          const WsHeader* __restrict__ hdr, int shift, uint32_t dmask, int nb) {
     __shared__ uint32_t whist[8][256];
     __shared__ uint32_t goff[256];
+    __shared__ uint32_t loff[256];  // first block-local position of each digit
+    __shared__ uint32_t wsum[8];
+    __shared__ unsigned long long sk[SORT_ITEMS];
+    __shared__ uint32_t sv[SORT_ITEMS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int j = threadIdx.x; j < 8 * 256; j += 256) (&whist[0][0])[j] = 0;
     goff[threadIdx.x] = scanned[(int64_t)threadIdx.x * nb + blockIdx.x];
     __syncthreads();
     const uint32_t n = n_valid(hdr);
-    const int64_t base = (int64_t)blockIdx.x * SORT_ITEMS + w * 256;
+    const int64_t block0 = (int64_t)blockIdx.x * SORT_ITEMS;
+    const int64_t base = block0 + w * 256;
     const uint32_t lt_mask = (1u << lane) - 1u;
     unsigned long long k[8];
     uint32_t v[8], rank[8], dig[8];
@@ -271,6 +279,8 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     {
+        // per digit: the warps' exclusive offsets within the digit, then an
+        // exclusive scan of the digit totals over the block
         const int d = threadIdx.x;
         uint32_t run = 0;
 #pragma unroll
@@ -279,16 +289,38 @@ __global__ void __launch_bounds__(256)
             whist[w2][d] = run;
             run += c;
         }
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t wp = 0;
+        for (int w2 = 0; w2 < w; ++w2) wp += wsum[w2];
+        loff[d] = wp + x - run;
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < 8; ++it) {
         const uint32_t d = dig[it];
         if (d < 256u) {
-            const uint32_t dst = goff[d] + whist[w][d] + rank[it];
-            kout[dst] = k[it];
-            vout[dst] = v[it];
+            const uint32_t lp = loff[d] + whist[w][d] + rank[it];
+            sk[lp] = k[it];
+            sv[lp] = v[it];
         }
+    }
+    __syncthreads();
+    // the valid pairs are a prefix of the block's chunk
+    const int64_t rem = (int64_t)n - block0;
+    const int cnt = rem <= 0 ? 0 : (rem < SORT_ITEMS ? (int)rem : SORT_ITEMS);
+    for (int j = threadIdx.x; j < cnt; j += 256) {
+        const unsigned long long key = sk[j];
+        const uint32_t d = (uint32_t)(key >> shift) & dmask;
+        const uint32_t dst = goff[d] + ((uint32_t)j - loff[d]);
+        kout[dst] = key;
+        vout[dst] = sv[j];
     }
 }
 
