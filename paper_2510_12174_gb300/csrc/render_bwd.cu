@@ -407,239 +407,341 @@ struct PreBwdParams {
     float lowpass;
 };
 
+// Threads per block of the preprocess backward (4 warps).
+constexpr int PREBWD_THREADS = 128;
+
+// The preprocess backward works warp by warp on 32 Gaussians.  Their
+// (camera, Gaussian) pairs with a kept tile are dealt to the warp's lanes 32
+// at a time, so that no lane idles on a camera that does not see its
+// Gaussian (about a third of the pairs have a kept tile); each pair's
+// contributions are added to the Gaussian's row of shared-memory
+// accumulators, which the Gaussian's own lane then maps onto the parameters.
 // DEG is the SH degree: with the basis size a compile-time constant the
-// basis, its gradient and the coefficient gradients are registers, not
-// local memory.  Three 128-thread blocks per SM (a few spilled registers at
-// degree 3) hide more load latency than two without spills.
+// basis, its gradient and the coefficient gradients are registers.
 template <int DEG>
-__global__ void __launch_bounds__(128, 3) preprocess_bwd_kernel(const PreBwdParams P) {
+__global__ void __launch_bounds__(PREBWD_THREADS) preprocess_bwd_kernel(const PreBwdParams P) {
     constexpr int n_sh = (DEG + 1) * (DEG + 1);
+    // accumulators per Gaussian: g_mu 3, g_R 9, g_s 3, g_th 3, g_op, g_k, g_sh
+    constexpr int NACC = 20 + 3 * n_sh;
+    constexpr int ACCS = NACC | 1;  // odd row stride: the lanes' rows start in different banks
+    constexpr int WARPS = PREBWD_THREADS / 32;
+    __shared__ float acc_all[WARPS][32 * ACCS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* acc = acc_all[wib];
     const int64_t n = P.g.n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float mu[3] = {P.g.mean[i], P.g.mean[n + i], P.g.mean[2 * n + i]};
-        const float q0[4] = {P.g.quat[i], P.g.quat[n + i], P.g.quat[2 * n + i],
-                             P.g.quat[3 * n + i]};
-        const float s[3] = {P.g.scale[i], P.g.scale[n + i], P.g.scale[2 * n + i]};
-        const float qn = sqrtf(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
-        const float iq = 1.f / qn;
-        const float w = q0[0] * iq, x = q0[1] * iq, y = q0[2] * iq, z = q0[3] * iq;
-        float R[3][3];
-        R[0][0] = 1.f - 2.f * (y * y + z * z);
-        R[0][1] = 2.f * (x * y - w * z);
-        R[0][2] = 2.f * (x * z + w * y);
-        R[1][0] = 2.f * (x * y + w * z);
-        R[1][1] = 1.f - 2.f * (x * x + z * z);
-        R[1][2] = 2.f * (y * z - w * x);
-        R[2][0] = 2.f * (x * z - w * y);
-        R[2][1] = 2.f * (y * z + w * x);
-        R[2][2] = 1.f - 2.f * (x * x + y * y);
-        const float is[3] = {1.f / s[0], 1.f / s[1], 1.f / s[2]};
-        float M[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) M[a][b] = R[a][b] * s[b];
-
-        float g_mu[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {}, g_s[3] = {0.f, 0.f, 0.f};
-        float g_th[3] = {0.f, 0.f, 0.f};  // rotation R -> R exp([theta]_x)
-        float g_op = 0.f, g_k = 0.f;
-        float g_sh[n_sh][3];
+    const int64_t stride = (int64_t)gridDim.x * WARPS * 32;
+    for (int64_t g0 = ((int64_t)blockIdx.x * WARPS + wib) * 32; g0 < n; g0 += stride) {
+        // the cameras with a kept tile of this lane's Gaussian
+        const int64_t own = g0 + lane;
+        uint64_t mask = 0;
+        if (own < n)
+            for (int k = 0; k < P.n_cams; ++k)
+                if (P.touched[(size_t)k * (size_t)n + (size_t)own]) mask |= 1ull << k;
+        for (int e = lane; e < 32 * ACCS; e += 32) acc[e] = 0.f;
+        const int cnt = __popcll(mask);
+        int incl = cnt;
 #pragma unroll
-        for (int k = 0; k < n_sh; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
-
-        for (int k = 0; k < P.n_cams; ++k) {
-            const size_t t = (size_t)k * (size_t)n + (size_t)i;
-            if (P.touched[t] == 0) continue;
-            const DevCam& cam = P.tab->cam[k];
-            float gr[GREC_FLOATS];
-            const double2* src = reinterpret_cast<const double2*>(P.grec + t * GREC_FLOATS);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int pre = incl - cnt;  // the lane's first pair in the warp's numbering
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (int r0 = 0; r0 < total; r0 += 32) {
+            const int q = r0 + lane;
+            // the pair's Gaussian: the last lane whose first pair is at or
+            // before q (pre is non-decreasing over the lanes)
+            int src = 0;
 #pragma unroll
-            for (int q = 0; q < GREC_FLOATS / 2; ++q) {
-                const double2 f = src[q];
-                gr[2 * q] = (float)f.x;
-                gr[2 * q + 1] = (float)f.y;
+            for (int step = 16; step > 0; step >>= 1) {
+                const int pc = __shfl_sync(0xffffffffu, pre, src + step);
+                if (pc <= q) src += step;
             }
-            g_op += gr[G_OP];
-            g_k += gr[G_K];
-
-            // ---- colour -> SH and viewing direction
-            {
-                float d[3] = {mu[0] - cam.C[0], mu[1] - cam.C[1], mu[2] - cam.C[2]};
-                const float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                const float il = 1.f / len;
-                d[0] *= il; d[1] *= il; d[2] *= il;
-                float Y[16];
-                sh_eval_basis(d[0], d[1], d[2], DEG, Y);
-                float dY[16][3];
-                sh_eval_basis_grad(d[0], d[1], d[2], DEG, dY);
-                float g_dir[3] = {0.f, 0.f, 0.f};
-                const size_t shb = (size_t)i * n_sh * 3;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float hc[n_sh];
-                    float raw = 0.5f;
-#pragma unroll
-                    for (int kk = 0; kk < n_sh; ++kk) {
-                        hc[kk] = load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype);
-                        raw = fmaf(Y[kk], hc[kk], raw);
-                    }
-                    if (raw < 0.f) continue;  // clamped at 0
-                    const float gc = gr[G_RGB + ch];
-#pragma unroll
-                    for (int kk = 0; kk < n_sh; ++kk) {
-                        g_sh[kk][ch] = fmaf(Y[kk], gc, g_sh[kk][ch]);
-                        const float h = hc[kk] * gc;
-                        g_dir[0] = fmaf(h, dY[kk][0], g_dir[0]);
-                        g_dir[1] = fmaf(h, dY[kk][1], g_dir[1]);
-                        g_dir[2] = fmaf(h, dY[kk][2], g_dir[2]);
-                    }
-                }
-                const float dd = g_dir[0] * d[0] + g_dir[1] * d[1] + g_dir[2] * d[2];
-                for (int a = 0; a < 3; ++a) g_mu[a] += (g_dir[a] - dd * d[a]) * il;
-            }
-
-            // ---- projection, EWA covariance, conic
-            const float* Wr = cam.R_wc;
-            const float pc[3] = {Wr[0] * mu[0] + Wr[1] * mu[1] + Wr[2] * mu[2] + cam.t_wc[0],
-                                 Wr[3] * mu[0] + Wr[4] * mu[1] + Wr[5] * mu[2] + cam.t_wc[1],
-                                 Wr[6] * mu[0] + Wr[7] * mu[1] + Wr[8] * mu[2] + cam.t_wc[2]};
-            const float iz = 1.f / pc[2];
-            const float J00 = cam.fx * iz, J11 = cam.fy * iz;
-            const float J02 = -cam.fx * pc[0] * iz * iz, J12 = -cam.fy * pc[1] * iz * iz;
-            float Tm[2][3];
-            for (int j = 0; j < 3; ++j) {
-                Tm[0][j] = J00 * Wr[j] + J02 * Wr[6 + j];
-                Tm[1][j] = J11 * Wr[3 + j] + J12 * Wr[6 + j];
-            }
-            // The record holds G' = dL/d(2D covariance) in the splat's
-            // principal frame E (columns e0 = (ec, es), e1 = (-es, ec)), so
-            // G = E G' E^T.  With V' = E^T T M (M = R S: the projected scaled
-            // axes in that frame) every product below stays free of
-            // cancellation, also for a thin splat seen far off-axis, where
-            // T^T G T has entries orders of magnitude above the gradients.
-            const float* rp = P.rec + t * REC_FLOATS;
-            const float ec = rp[R_EC], es = rp[R_ES];
-            // the long-axis row in float32 here; the short-axis row, orders of
-            // magnitude below T M's entries for a thin splat seen far
-            // off-axis, from the preprocess's double-float chain
-            float Vp[2][3];
-            {
-                const float4 v1 = P.vp[t];
-                Vp[1][0] = v1.x;
-                Vp[1][1] = v1.y;
-                Vp[1][2] = v1.z;
-            }
-            for (int j = 0; j < 3; ++j) {
-                float tm[2];
-                for (int a = 0; a < 2; ++a)
-                    tm[a] = Tm[a][0] * M[0][j] + Tm[a][1] * M[1][j] + Tm[a][2] * M[2][j];
-                Vp[0][j] = ec * tm[0] + es * tm[1];
-            }
-            const float Gp[2][2] = {{gr[G_CA], 0.5f * gr[G_CB]}, {0.5f * gr[G_CB], gr[G_CC]}};
-            float GV[2][3];
-            for (int a = 0; a < 2; ++a)
-                for (int j = 0; j < 3; ++j) GV[a][j] = Gp[a][0] * Vp[0][j] + Gp[a][1] * Vp[1][j];
-            // H = V'^T G' V' = S (T R)^T G (T R) S.  Sigma = R S^2 R^T:
-            // dL/ds_b = 2 H_bb / s_b, and for R -> R exp([theta]_x)
-            // dL/dtheta_k = 2 (s_i / s_j - s_j / s_i) H_ij, (i, j, k) cyclic
-            float H[3][3];
+            const uint32_t mlo = __shfl_sync(0xffffffffu, (uint32_t)mask, src);
+            const uint32_t mhi = __shfl_sync(0xffffffffu, (uint32_t)(mask >> 32), src);
+            const int psrc = __shfl_sync(0xffffffffu, pre, src);
+            if (q >= total) continue;  // no shuffle follows in this round
+            // its camera: set bit number q - psrc of the Gaussian's mask
+            uint64_t mm = ((uint64_t)mhi << 32) | mlo;
+            for (int j = q - psrc; j > 0; --j) mm &= mm - 1;
+            const int k = __ffsll((long long)mm) - 1;
+            const int64_t i = g0 + src;
+            const float mu[3] = {P.g.mean[i], P.g.mean[n + i], P.g.mean[2 * n + i]};
+            const float q0[4] = {P.g.quat[i], P.g.quat[n + i], P.g.quat[2 * n + i],
+                                 P.g.quat[3 * n + i]};
+            const float s[3] = {P.g.scale[i], P.g.scale[n + i], P.g.scale[2 * n + i]};
+            const float qn = sqrtf(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
+            const float iq = 1.f / qn;
+            const float w = q0[0] * iq, x = q0[1] * iq, y = q0[2] * iq, z = q0[3] * iq;
+            float R[3][3];
+            R[0][0] = 1.f - 2.f * (y * y + z * z);
+            R[0][1] = 2.f * (x * y - w * z);
+            R[0][2] = 2.f * (x * z + w * y);
+            R[1][0] = 2.f * (x * y + w * z);
+            R[1][1] = 1.f - 2.f * (x * x + z * z);
+            R[1][2] = 2.f * (y * z - w * x);
+            R[2][0] = 2.f * (x * z - w * y);
+            R[2][1] = 2.f * (y * z + w * x);
+            R[2][2] = 1.f - 2.f * (x * x + y * y);
+            const float is[3] = {1.f / s[0], 1.f / s[1], 1.f / s[2]};
+            float M[3][3];
             for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) H[a][b] = Vp[0][a] * GV[0][b] + Vp[1][a] * GV[1][b];
-            for (int b = 0; b < 3; ++b) g_s[b] += 2.f * H[b][b] * is[b];
-            g_th[0] += 2.f * (s[1] * is[2] - s[2] * is[1]) * H[1][2];
-            g_th[1] += 2.f * (s[2] * is[0] - s[0] * is[2]) * H[2][0];
-            g_th[2] += 2.f * (s[0] * is[1] - s[1] * is[0]) * H[0][1];
-            // dL/dT = 2 G T Sigma = 2 E (G' V') M^T
-            float gT[2][3];
+                for (int b = 0; b < 3; ++b) M[a][b] = R[a][b] * s[b];
+
+            float g_mu[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {}, g_s[3] = {0.f, 0.f, 0.f};
+            float g_th[3] = {0.f, 0.f, 0.f};  // rotation R -> R exp([theta]_x)
+            float g_op = 0.f, g_k = 0.f;
+            float g_sh[n_sh][3];
+#pragma unroll
+            for (int kk = 0; kk < n_sh; ++kk) g_sh[kk][0] = g_sh[kk][1] = g_sh[kk][2] = 0.f;
             {
-                float EGV[2][3];
+                const size_t t = (size_t)k * (size_t)n + (size_t)i;
+                const DevCam& cam = P.tab->cam[k];
+                float gr[GREC_FLOATS];
+                const double2* src = reinterpret_cast<const double2*>(P.grec + t * GREC_FLOATS);
+    #pragma unroll
+                for (int q = 0; q < GREC_FLOATS / 2; ++q) {
+                    const double2 f = src[q];
+                    gr[2 * q] = (float)f.x;
+                    gr[2 * q + 1] = (float)f.y;
+                }
+                g_op += gr[G_OP];
+                g_k += gr[G_K];
+
+                // ---- colour -> SH and viewing direction
+                {
+                    float d[3] = {mu[0] - cam.C[0], mu[1] - cam.C[1], mu[2] - cam.C[2]};
+                    const float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    const float il = 1.f / len;
+                    d[0] *= il; d[1] *= il; d[2] *= il;
+                    float Y[16];
+                    sh_eval_basis(d[0], d[1], d[2], DEG, Y);
+                    float dY[16][3];
+                    sh_eval_basis_grad(d[0], d[1], d[2], DEG, dY);
+                    float g_dir[3] = {0.f, 0.f, 0.f};
+                    const size_t shb = (size_t)i * n_sh * 3;
+    #pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        float hc[n_sh];
+                        float raw = 0.5f;
+    #pragma unroll
+                        for (int kk = 0; kk < n_sh; ++kk) {
+                            hc[kk] = load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype);
+                            raw = fmaf(Y[kk], hc[kk], raw);
+                        }
+                        if (raw < 0.f) continue;  // clamped at 0
+                        const float gc = gr[G_RGB + ch];
+    #pragma unroll
+                        for (int kk = 0; kk < n_sh; ++kk) {
+                            g_sh[kk][ch] = fmaf(Y[kk], gc, g_sh[kk][ch]);
+                            const float h = hc[kk] * gc;
+                            g_dir[0] = fmaf(h, dY[kk][0], g_dir[0]);
+                            g_dir[1] = fmaf(h, dY[kk][1], g_dir[1]);
+                            g_dir[2] = fmaf(h, dY[kk][2], g_dir[2]);
+                        }
+                    }
+                    const float dd = g_dir[0] * d[0] + g_dir[1] * d[1] + g_dir[2] * d[2];
+                    for (int a = 0; a < 3; ++a) g_mu[a] += (g_dir[a] - dd * d[a]) * il;
+                }
+
+                // ---- projection, EWA covariance, conic
+                const float* Wr = cam.R_wc;
+                const float pc[3] = {Wr[0] * mu[0] + Wr[1] * mu[1] + Wr[2] * mu[2] + cam.t_wc[0],
+                                     Wr[3] * mu[0] + Wr[4] * mu[1] + Wr[5] * mu[2] + cam.t_wc[1],
+                                     Wr[6] * mu[0] + Wr[7] * mu[1] + Wr[8] * mu[2] + cam.t_wc[2]};
+                const float iz = 1.f / pc[2];
+                const float J00 = cam.fx * iz, J11 = cam.fy * iz;
+                const float J02 = -cam.fx * pc[0] * iz * iz, J12 = -cam.fy * pc[1] * iz * iz;
+                float Tm[2][3];
                 for (int j = 0; j < 3; ++j) {
-                    EGV[0][j] = ec * GV[0][j] - es * GV[1][j];
-                    EGV[1][j] = es * GV[0][j] + ec * GV[1][j];
+                    Tm[0][j] = J00 * Wr[j] + J02 * Wr[6 + j];
+                    Tm[1][j] = J11 * Wr[3 + j] + J12 * Wr[6 + j];
                 }
+                // The record holds G' = dL/d(2D covariance) in the splat's
+                // principal frame E (columns e0 = (ec, es), e1 = (-es, ec)), so
+                // G = E G' E^T.  With V' = E^T T M (M = R S: the projected scaled
+                // axes in that frame) every product below stays free of
+                // cancellation, also for a thin splat seen far off-axis, where
+                // T^T G T has entries orders of magnitude above the gradients.
+                const float* rp = P.rec + t * REC_FLOATS;
+                const float ec = rp[R_EC], es = rp[R_ES];
+                // the long-axis row in float32 here; the short-axis row, orders of
+                // magnitude below T M's entries for a thin splat seen far
+                // off-axis, from the preprocess's double-float chain
+                float Vp[2][3];
+                {
+                    const float4 v1 = P.vp[t];
+                    Vp[1][0] = v1.x;
+                    Vp[1][1] = v1.y;
+                    Vp[1][2] = v1.z;
+                }
+                for (int j = 0; j < 3; ++j) {
+                    float tm[2];
+                    for (int a = 0; a < 2; ++a)
+                        tm[a] = Tm[a][0] * M[0][j] + Tm[a][1] * M[1][j] + Tm[a][2] * M[2][j];
+                    Vp[0][j] = ec * tm[0] + es * tm[1];
+                }
+                const float Gp[2][2] = {{gr[G_CA], 0.5f * gr[G_CB]}, {0.5f * gr[G_CB], gr[G_CC]}};
+                float GV[2][3];
                 for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 3; ++b)
-                        gT[a][b] = 2.f * (EGV[a][0] * M[b][0] + EGV[a][1] * M[b][1] +
-                                          EGV[a][2] * M[b][2]);
-            }
-            const float gJ00 = gT[0][0] * Wr[0] + gT[0][1] * Wr[1] + gT[0][2] * Wr[2];
-            const float gJ02 = gT[0][0] * Wr[6] + gT[0][1] * Wr[7] + gT[0][2] * Wr[8];
-            const float gJ11 = gT[1][0] * Wr[3] + gT[1][1] * Wr[4] + gT[1][2] * Wr[5];
-            const float gJ12 = gT[1][0] * Wr[6] + gT[1][1] * Wr[7] + gT[1][2] * Wr[8];
-            float g_pc[3];
-            g_pc[0] = gJ02 * (-cam.fx * iz * iz) + gr[G_MX] * cam.fx * iz;
-            g_pc[1] = gJ12 * (-cam.fy * iz * iz) + gr[G_MY] * cam.fy * iz;
-            g_pc[2] = -gJ00 * cam.fx * iz * iz + gJ02 * 2.f * cam.fx * pc[0] * iz * iz * iz -
-                      gJ11 * cam.fy * iz * iz + gJ12 * 2.f * cam.fy * pc[1] * iz * iz * iz -
-                      gr[G_MX] * cam.fx * pc[0] * iz * iz - gr[G_MY] * cam.fy * pc[1] * iz * iz +
-                      gr[G_Z];
-            for (int a = 0; a < 3; ++a)
-                g_mu[a] += Wr[a] * g_pc[0] + Wr[3 + a] * g_pc[1] + Wr[6 + a] * g_pc[2];
-
-            // ---- ray-ellipsoid setup (Sec. 3.2): v_s = S^-1 R^T (C - mu) and
-            // d_s = S^-1 R^T d.  The record holds g_vs and B (= g_vs (x) v_s +
-            // g_ds (x) d_s, accumulated in a form free of cancellation), so
-            //   dL/ds_a = -B[a][a] / s_a,
-            //   dL/dtheta_k = sum_ij eps_ijk (s_j / s_i) B[i][j],
-            //   dL/dmu = -R (g_vs / s).
-            {
-                const float* Bm = gr + G_B;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) g_s[a] -= Bm[4 * a] * is[a];
-                g_th[0] += s[2] * is[1] * Bm[5] - s[1] * is[2] * Bm[7];
-                g_th[1] += s[0] * is[2] * Bm[6] - s[2] * is[0] * Bm[2];
-                g_th[2] += s[1] * is[0] * Bm[1] - s[0] * is[1] * Bm[3];
-                for (int kk = 0; kk < 3; ++kk)
-                    g_mu[kk] -= R[kk][0] * gr[G_VS] * is[0] + R[kk][1] * gr[G_VS + 1] * is[1] +
-                                R[kk][2] * gr[G_VS + 2] * is[2];
-            }
-            // N_w[a][b] = R[a][b] / s_b
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    const float gnw = gr[G_NW + 3 * a + b];
-                    g_R[a][b] += gnw * is[b];
-                    g_s[b] -= gnw * R[a][b] * is[b] * is[b];
+                    for (int j = 0; j < 3; ++j) GV[a][j] = Gp[a][0] * Vp[0][j] + Gp[a][1] * Vp[1][j];
+                // H = V'^T G' V' = S (T R)^T G (T R) S.  Sigma = R S^2 R^T:
+                // dL/ds_b = 2 H_bb / s_b, and for R -> R exp([theta]_x)
+                // dL/dtheta_k = 2 (s_i / s_j - s_j / s_i) H_ij, (i, j, k) cyclic
+                float H[3][3];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) H[a][b] = Vp[0][a] * GV[0][b] + Vp[1][a] * GV[1][b];
+                for (int b = 0; b < 3; ++b) g_s[b] += 2.f * H[b][b] * is[b];
+                g_th[0] += 2.f * (s[1] * is[2] - s[2] * is[1]) * H[1][2];
+                g_th[1] += 2.f * (s[2] * is[0] - s[0] * is[2]) * H[2][0];
+                g_th[2] += 2.f * (s[0] * is[1] - s[1] * is[0]) * H[0][1];
+                // dL/dT = 2 G T Sigma = 2 E (G' V') M^T
+                float gT[2][3];
+                {
+                    float EGV[2][3];
+                    for (int j = 0; j < 3; ++j) {
+                        EGV[0][j] = ec * GV[0][j] - es * GV[1][j];
+                        EGV[1][j] = es * GV[0][j] + ec * GV[1][j];
+                    }
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            gT[a][b] = 2.f * (EGV[a][0] * M[b][0] + EGV[a][1] * M[b][1] +
+                                              EGV[a][2] * M[b][2]);
                 }
-        }
+                const float gJ00 = gT[0][0] * Wr[0] + gT[0][1] * Wr[1] + gT[0][2] * Wr[2];
+                const float gJ02 = gT[0][0] * Wr[6] + gT[0][1] * Wr[7] + gT[0][2] * Wr[8];
+                const float gJ11 = gT[1][0] * Wr[3] + gT[1][1] * Wr[4] + gT[1][2] * Wr[5];
+                const float gJ12 = gT[1][0] * Wr[6] + gT[1][1] * Wr[7] + gT[1][2] * Wr[8];
+                float g_pc[3];
+                g_pc[0] = gJ02 * (-cam.fx * iz * iz) + gr[G_MX] * cam.fx * iz;
+                g_pc[1] = gJ12 * (-cam.fy * iz * iz) + gr[G_MY] * cam.fy * iz;
+                g_pc[2] = -gJ00 * cam.fx * iz * iz + gJ02 * 2.f * cam.fx * pc[0] * iz * iz * iz -
+                          gJ11 * cam.fy * iz * iz + gJ12 * 2.f * cam.fy * pc[1] * iz * iz * iz -
+                          gr[G_MX] * cam.fx * pc[0] * iz * iz - gr[G_MY] * cam.fy * pc[1] * iz * iz +
+                          gr[G_Z];
+                for (int a = 0; a < 3; ++a)
+                    g_mu[a] += Wr[a] * g_pc[0] + Wr[3 + a] * g_pc[1] + Wr[6 + a] * g_pc[2];
 
-        // the rotation's local-frame gradient as a matrix gradient:
-        // 1/2 R [g_theta]_x has the same derivative along every tangent R [e]_x
-        {
-            const float K[3][3] = {{0.f, -g_th[2], g_th[1]},
-                                   {g_th[2], 0.f, -g_th[0]},
-                                   {-g_th[1], g_th[0], 0.f}};
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b)
-                    g_R[a][b] += 0.5f * (R[a][0] * K[0][b] + R[a][1] * K[1][b] + R[a][2] * K[2][b]);
+                // ---- ray-ellipsoid setup (Sec. 3.2): v_s = S^-1 R^T (C - mu) and
+                // d_s = S^-1 R^T d.  The record holds g_vs and B (= g_vs (x) v_s +
+                // g_ds (x) d_s, accumulated in a form free of cancellation), so
+                //   dL/ds_a = -B[a][a] / s_a,
+                //   dL/dtheta_k = sum_ij eps_ijk (s_j / s_i) B[i][j],
+                //   dL/dmu = -R (g_vs / s).
+                {
+                    const float* Bm = gr + G_B;
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a) g_s[a] -= Bm[4 * a] * is[a];
+                    g_th[0] += s[2] * is[1] * Bm[5] - s[1] * is[2] * Bm[7];
+                    g_th[1] += s[0] * is[2] * Bm[6] - s[2] * is[0] * Bm[2];
+                    g_th[2] += s[1] * is[0] * Bm[1] - s[0] * is[1] * Bm[3];
+                    for (int kk = 0; kk < 3; ++kk)
+                        g_mu[kk] -= R[kk][0] * gr[G_VS] * is[0] + R[kk][1] * gr[G_VS + 1] * is[1] +
+                                    R[kk][2] * gr[G_VS + 2] * is[2];
+                }
+                // N_w[a][b] = R[a][b] / s_b
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        const float gnw = gr[G_NW + 3 * a + b];
+                        g_R[a][b] += gnw * is[b];
+                        g_s[b] -= gnw * R[a][b] * is[b] * is[b];
+                    }
+            }
+            // this pair's share of the Gaussian's sums
+            float* row = acc + src * ACCS;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                atomicAdd(row + a, g_mu[a]);
+                atomicAdd(row + 12 + a, g_s[a]);
+                atomicAdd(row + 15 + a, g_th[a]);
+#pragma unroll
+                for (int b = 0; b < 3; ++b) atomicAdd(row + 3 + 3 * a + b, g_R[a][b]);
+            }
+            atomicAdd(row + 18, g_op);
+            atomicAdd(row + 19, g_k);
+#pragma unroll
+            for (int kk = 0; kk < n_sh; ++kk)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) atomicAdd(row + 20 + 3 * kk + ch, g_sh[kk][ch]);
         }
-        // R(q^) -> q^ -> q
-        const float gw = 2.f * (-z * g_R[0][1] + y * g_R[0][2] + z * g_R[1][0] - x * g_R[1][2] -
-                                y * g_R[2][0] + x * g_R[2][1]);
-        const float gx = 2.f * (y * g_R[0][1] + z * g_R[0][2] + y * g_R[1][0] - 2.f * x * g_R[1][1] -
-                                w * g_R[1][2] + z * g_R[2][0] + w * g_R[2][1] - 2.f * x * g_R[2][2]);
-        const float gy = 2.f * (-2.f * y * g_R[0][0] + x * g_R[0][1] + w * g_R[0][2] + x * g_R[1][0] +
-                                z * g_R[1][2] - w * g_R[2][0] + z * g_R[2][1] - 2.f * y * g_R[2][2]);
-        const float gz = 2.f * (-2.f * z * g_R[0][0] - w * g_R[0][1] + x * g_R[0][2] + w * g_R[1][0] -
-                                2.f * z * g_R[1][1] + y * g_R[1][2] + x * g_R[2][0] + y * g_R[2][1]);
-        const float dq = gw * w + gx * x + gy * y + gz * z;
-        const float g_q[4] = {(gw - dq * w) * iq, (gx - dq * x) * iq, (gy - dq * y) * iq,
-                              (gz - dq * z) * iq};
+        __syncwarp();
+        if (own < n) {
+            const int64_t i = own;
+            const float q0[4] = {P.g.quat[i], P.g.quat[n + i], P.g.quat[2 * n + i],
+                                 P.g.quat[3 * n + i]};
+            const float qn = sqrtf(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
+            const float iq = 1.f / qn;
+            const float w = q0[0] * iq, x = q0[1] * iq, y = q0[2] * iq, z = q0[3] * iq;
+            float R[3][3];
+            R[0][0] = 1.f - 2.f * (y * y + z * z);
+            R[0][1] = 2.f * (x * y - w * z);
+            R[0][2] = 2.f * (x * z + w * y);
+            R[1][0] = 2.f * (x * y + w * z);
+            R[1][1] = 1.f - 2.f * (x * x + z * z);
+            R[1][2] = 2.f * (y * z - w * x);
+            R[2][0] = 2.f * (x * z - w * y);
+            R[2][1] = 2.f * (y * z + w * x);
+            R[2][2] = 1.f - 2.f * (x * x + y * y);
+            const float* row = acc + lane * ACCS;
+            float g_mu[3], g_R[3][3], g_s[3], g_th[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                g_mu[a] = row[a];
+                g_s[a] = row[12 + a];
+                g_th[a] = row[15 + a];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) g_R[a][b] = row[3 + 3 * a + b];
+            }
+            const float g_op = row[18], g_k = row[19];
+            float g_sh[n_sh][3];
+#pragma unroll
+            for (int kk = 0; kk < n_sh; ++kk)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) g_sh[kk][ch] = row[20 + 3 * kk + ch];
+            // the rotation's local-frame gradient as a matrix gradient:
+            // 1/2 R [g_theta]_x has the same derivative along every tangent R [e]_x
+            {
+                const float K[3][3] = {{0.f, -g_th[2], g_th[1]},
+                                       {g_th[2], 0.f, -g_th[0]},
+                                       {-g_th[1], g_th[0], 0.f}};
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        g_R[a][b] += 0.5f * (R[a][0] * K[0][b] + R[a][1] * K[1][b] + R[a][2] * K[2][b]);
+            }
+            // R(q^) -> q^ -> q
+            const float gw = 2.f * (-z * g_R[0][1] + y * g_R[0][2] + z * g_R[1][0] - x * g_R[1][2] -
+                                    y * g_R[2][0] + x * g_R[2][1]);
+            const float gx = 2.f * (y * g_R[0][1] + z * g_R[0][2] + y * g_R[1][0] - 2.f * x * g_R[1][1] -
+                                    w * g_R[1][2] + z * g_R[2][0] + w * g_R[2][1] - 2.f * x * g_R[2][2]);
+            const float gy = 2.f * (-2.f * y * g_R[0][0] + x * g_R[0][1] + w * g_R[0][2] + x * g_R[1][0] +
+                                    z * g_R[1][2] - w * g_R[2][0] + z * g_R[2][1] - 2.f * y * g_R[2][2]);
+            const float gz = 2.f * (-2.f * z * g_R[0][0] - w * g_R[0][1] + x * g_R[0][2] + w * g_R[1][0] -
+                                    2.f * z * g_R[1][1] + y * g_R[1][2] + x * g_R[2][0] + y * g_R[2][1]);
+            const float dq = gw * w + gx * x + gy * y + gz * z;
+            const float g_q[4] = {(gw - dq * w) * iq, (gx - dq * x) * iq, (gy - dq * y) * iq,
+                                  (gz - dq * z) * iq};
 
-        const unigs_param_grads& O = P.out;
-        const bool acc = O.accumulate != 0;
-#define PUT(ptr, j, val) \
-    do { if (ptr) { if (acc) (ptr)[j] += (val); else (ptr)[j] = (val); } } while (0)
-        for (int a = 0; a < 3; ++a) {
-            PUT(O.mean, a * n + i, g_mu[a]);
-            PUT(O.scale, a * n + i, g_s[a]);
+            const unigs_param_grads& O = P.out;
+            const bool acc = O.accumulate != 0;
+    #define PUT(ptr, j, val) \
+        do { if (ptr) { if (acc) (ptr)[j] += (val); else (ptr)[j] = (val); } } while (0)
+            for (int a = 0; a < 3; ++a) {
+                PUT(O.mean, a * n + i, g_mu[a]);
+                PUT(O.scale, a * n + i, g_s[a]);
+            }
+            for (int a = 0; a < 4; ++a) PUT(O.quat, a * n + i, g_q[a]);
+            PUT(O.opacity, i, g_op);
+            PUT(O.kfac, i, g_k);
+    #pragma unroll
+            for (int kk = 0; kk < n_sh; ++kk)
+    #pragma unroll
+                for (int ch = 0; ch < 3; ++ch) PUT(O.sh, ((size_t)i * n_sh + kk) * 3 + ch, g_sh[kk][ch]);
+    #undef PUT
         }
-        for (int a = 0; a < 4; ++a) PUT(O.quat, a * n + i, g_q[a]);
-        PUT(O.opacity, i, g_op);
-        PUT(O.kfac, i, g_k);
-#pragma unroll
-        for (int kk = 0; kk < n_sh; ++kk)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) PUT(O.sh, ((size_t)i * n_sh + kk) * 3 + ch, g_sh[kk][ch]);
-#undef PUT
+        // the rows are rewritten for the next 32 Gaussians only after every
+        // lane has read its own
+        __syncwarp();
     }
 }
 
@@ -738,14 +840,14 @@ int launch_render_bwd(const unigs_plan& p, const unigs_gaussians& g, void* ws,
         Q.touched = ws_ptr<uint32_t>(ws, p, OFF_TOUCH);
         Q.out = grads;
         Q.lowpass = p.cfg.lowpass;
-        const int64_t blocks = (p.n + 127) / 128;
+        const int64_t blocks = (p.n + PREBWD_THREADS - 1) / PREBWD_THREADS;
         const int64_t cap = (int64_t)sm_count() * 32;
         const int grid = (int)(blocks < cap ? blocks : cap);
         switch (g.sh_degree) {
-            case 0: preprocess_bwd_kernel<0><<<grid, 128, 0, st>>>(Q); break;
-            case 1: preprocess_bwd_kernel<1><<<grid, 128, 0, st>>>(Q); break;
-            case 2: preprocess_bwd_kernel<2><<<grid, 128, 0, st>>>(Q); break;
-            default: preprocess_bwd_kernel<3><<<grid, 128, 0, st>>>(Q); break;
+            case 0: preprocess_bwd_kernel<0><<<grid, PREBWD_THREADS, 0, st>>>(Q); break;
+            case 1: preprocess_bwd_kernel<1><<<grid, PREBWD_THREADS, 0, st>>>(Q); break;
+            case 2: preprocess_bwd_kernel<2><<<grid, PREBWD_THREADS, 0, st>>>(Q); break;
+            default: preprocess_bwd_kernel<3><<<grid, PREBWD_THREADS, 0, st>>>(Q); break;
         }
         ++launches;
     }
