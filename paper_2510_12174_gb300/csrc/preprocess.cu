@@ -555,7 +555,7 @@ int launch_preprocess(const unigs_plan& p, const unigs_gaussians& g, const CamTa
             p.cfg.lowpass, ws_ptr<uint2>(ws, p, OFF_RECT), ws_ptr<uint32_t>(ws, p, OFF_TOUCH),
             ws_ptr<uint32_t>(ws, p, OFF_ZBITS), ws_ptr<float>(ws, p, OFF_CULL), hdr, kept_list);
         // grid-stride over the list, whose length only the device knows
-        const int64_t cap2 = (int64_t)sm_count() * 8;
+        const int64_t cap2 = (int64_t)sm_count() * 32;
         const int grid2 = (int)(blocks < cap2 ? blocks : cap2);
         preprocess_splat_kernel<<<grid2, 256, 0, st>>>(
             g, ws_ptr<CamTable>(ws, p, OFF_CAM), p.cfg.lowpass, kept_list, hdr,

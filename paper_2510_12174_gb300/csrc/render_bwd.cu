@@ -417,9 +417,11 @@ constexpr int PREBWD_THREADS = 128;
 // contributions are added to the Gaussian's row of shared-memory
 // accumulators, which the Gaussian's own lane then maps onto the parameters.
 // DEG is the SH degree: with the basis size a compile-time constant the
-// basis, its gradient and the coefficient gradients are registers.
+// basis, its gradient and the coefficient gradients are registers.  Four
+// blocks per SM (a few spilled registers at degree 3) measured faster than
+// three without spills.
 template <int DEG>
-__global__ void __launch_bounds__(PREBWD_THREADS) preprocess_bwd_kernel(const PreBwdParams P) {
+__global__ void __launch_bounds__(PREBWD_THREADS, 4) preprocess_bwd_kernel(const PreBwdParams P) {
     constexpr int n_sh = (DEG + 1) * (DEG + 1);
     // accumulators per Gaussian: g_mu 3, g_R 9, g_s 3, g_th 3, g_op, g_k, g_sh
     constexpr int NACC = 20 + 3 * n_sh;
