@@ -120,7 +120,7 @@ class ClockSampler:
 BWD_TRAFFIC_BYTES = 8_011_275_264
 BWD_TRAFFIC_SOURCES = ('render_bwd.cu', 'render_bwd_tc.cu', 'bwd_pair.cuh', 'splat.cuh',
                        'unigs_internal.cuh', 'ff.cuh', 'sh.cuh', 'tcgen05.cuh', 'ewa_ff.cuh')
-BWD_TRAFFIC_DIGEST = "00c96014ff079846864035089f7f7f60ca29fb9a939fcd07e378dc913b67d628"
+BWD_TRAFFIC_DIGEST = "17fa63418f3ab9ddaa7db3a63fab7763aa46e23baf9dbbefadb36cd10529797d"
 
 
 def bwd_traffic():

@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(PREBWD_THREADS, 4) preprocess_bwd_kernel(const
                 const DevCam& cam = P.tab->cam[k];
                 float gr[GREC_FLOATS];
                 const double2* src = reinterpret_cast<const double2*>(P.grec + t * GREC_FLOATS);
-    #pragma unroll
+#pragma unroll
                 for (int q = 0; q < GREC_FLOATS / 2; ++q) {
                     const double2 f = src[q];
                     gr[2 * q] = (float)f.x;
@@ -523,18 +523,18 @@ __global__ void __launch_bounds__(PREBWD_THREADS, 4) preprocess_bwd_kernel(const
                     sh_eval_basis_grad(d[0], d[1], d[2], DEG, dY);
                     float g_dir[3] = {0.f, 0.f, 0.f};
                     const size_t shb = (size_t)i * n_sh * 3;
-    #pragma unroll
+#pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
                         float hc[n_sh];
                         float raw = 0.5f;
-    #pragma unroll
+#pragma unroll
                         for (int kk = 0; kk < n_sh; ++kk) {
                             hc[kk] = load_feat(P.g.sh, shb + kk * 3 + ch, P.g.feat_dtype);
                             raw = fmaf(Y[kk], hc[kk], raw);
                         }
                         if (raw < 0.f) continue;  // clamped at 0
                         const float gc = gr[G_RGB + ch];
-    #pragma unroll
+#pragma unroll
                         for (int kk = 0; kk < n_sh; ++kk) {
                             g_sh[kk][ch] = fmaf(Y[kk], gc, g_sh[kk][ch]);
                             const float h = hc[kk] * gc;
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(PREBWD_THREADS, 4) preprocess_bwd_kernel(const
                 //   dL/dmu = -R (g_vs / s).
                 {
                     const float* Bm = gr + G_B;
-    #pragma unroll
+#pragma unroll
                     for (int a = 0; a < 3; ++a) g_s[a] -= Bm[4 * a] * is[a];
                     g_th[0] += s[2] * is[1] * Bm[5] - s[1] * is[2] * Bm[7];
                     g_th[1] += s[0] * is[2] * Bm[6] - s[2] * is[0] * Bm[2];
@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(PREBWD_THREADS, 4) preprocess_bwd_kernel(const
 
             const unigs_param_grads& O = P.out;
             const bool acc = O.accumulate != 0;
-    #define PUT(ptr, j, val) \
+#define PUT(ptr, j, val) \
         do { if (ptr) { if (acc) (ptr)[j] += (val); else (ptr)[j] = (val); } } while (0)
             for (int a = 0; a < 3; ++a) {
                 PUT(O.mean, a * n + i, g_mu[a]);
@@ -735,11 +735,11 @@ __global__ void __launch_bounds__(PREBWD_THREADS, 4) preprocess_bwd_kernel(const
             for (int a = 0; a < 4; ++a) PUT(O.quat, a * n + i, g_q[a]);
             PUT(O.opacity, i, g_op);
             PUT(O.kfac, i, g_k);
-    #pragma unroll
+#pragma unroll
             for (int kk = 0; kk < n_sh; ++kk)
-    #pragma unroll
+#pragma unroll
                 for (int ch = 0; ch < 3; ++ch) PUT(O.sh, ((size_t)i * n_sh + kk) * 3 + ch, g_sh[kk][ch]);
-    #undef PUT
+#undef PUT
         }
         // the rows are rewritten for the next 32 Gaussians only after every
         // lane has read its own
