@@ -211,20 +211,25 @@ void unigs_config_default(unigs_config* cfg);
  * duplication step); 0 picks 4 * n * n_cams.  cams is host memory.  The
  * plan's cfg holds the resolved tile shape (16 x 16 for 0 x 0).
  * Returns UNIGS_ERR_INVALID_ARG on n < 0, n_cams outside 1..UNIGS_MAX_CAMS,
- * an empty image, sh_degree outside 0..3, n_sem outside 0..64, a tile shape
- * other than the four listed in unigs_config. */
+ * n * n_cams >= 2^32 (the device lists index (camera, Gaussian) pairs in 32
+ * bits; the workspace, over 500 bytes a pair, would not fit anyway), an empty
+ * image, sh_degree outside 0..3, n_sem outside 0..64, a tile shape other than
+ * the four listed in unigs_config. */
 unigs_status unigs_plan_init(unigs_plan* plan, const unigs_gaussians* g,
                              const unigs_camera* cams, int32_t n_cams,
                              const unigs_config* cfg, int64_t instance_capacity);
 
 size_t unigs_workspace_bytes(const unigs_plan* plan);
 
-/* Preprocess (per camera x Gaussian, one thread each): projection, EWA 2D
+/* Preprocess (per camera x Gaussian): projection, EWA 2D
  * covariance with the low-pass, 3-sigma tile rectangle, SH colour, the
  * per-Gaussian ray-ellipsoid setup of Sec. 3.2 (v_s = S^-1 R^T (C - mu) and
  * the camera-ray map S^-1 R^T R_cw) and the depth key.  The tile rectangle
- * and key follow an explicit float32 recipe (bit-reproducible).  Also clears
- * the workspace status word.  cams: host array of plan->n_cams cameras.
+ * and key follow an explicit float32 recipe (bit-reproducible).  Two passes:
+ * the culling pass (one thread per pair) decides the tiles and lists the
+ * pairs with a kept tile; the splat pass (one thread per listed pair) writes
+ * their records.  Also clears the workspace status word.  cams: host array of
+ * plan->n_cams cameras.
  * With UNIGS_FLAG_CHECK_FINITE it first scans the Gaussian arrays for NaN
  * and infinity (UNIGS_ERR_NONFINITE in the status word; the stages still run,
  * and a non-finite input then gives non-finite outputs, never a hang). */

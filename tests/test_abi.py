@@ -66,6 +66,13 @@ def test_plan_rejects_bad_arguments_on_host(lib):
     bad = rz.make_cameras(cams)
     bad[0].width = 0
     assert lib.unigs_plan_init(plan, g, bad, 1, None, 0) == lib.UNIGS_ERR_INVALID_ARG
+    # (camera, Gaussian) pair indices are 32-bit in the device lists
+    arr3 = rz.make_cameras([cams[0]] * 3)
+    g.n = 2 ** 31 - 1
+    assert lib.unigs_plan_init(plan, g, arr3, 3, None, 0) == lib.UNIGS_ERR_INVALID_ARG
+    g.n = 2 ** 31 - 1
+    assert lib.unigs_plan_init(plan, g, arr3, 2, None, 0) == lib.UNIGS_OK  # 2^32 - 2 pairs
+    g.n = 10
     # entry points reject NULL / mismatched arguments before touching the GPU
     assert lib.unigs_plan_init(plan, g, arr, 1, None, 0) == lib.UNIGS_OK
     assert lib.unigs_preprocess(plan, g, arr, None, None) == lib.UNIGS_ERR_INVALID_ARG
