@@ -225,6 +225,22 @@ def test_sh_degrees_forward_and_backward(deg):
     check_grad_errors(_grad_case(sc, cams, seed=50 + deg))
 
 
+def test_backward_parity_forty_cameras():
+    """40 cameras: the preprocess backward tracks each Gaussian's cameras
+    with a kept tile in a 64-bit mask and deals the pairs to its warp's
+    lanes, so cameras 32-39 take the mask's upper word (a camera dropped or
+    taken twice would put errors of the order of the RMS on the Gaussians it
+    sees).  A centre gradient here sums up to 40 per-camera terms, each a
+    float32 sum over pixels; where the total cancels far below the RMS it
+    keeps their float32 error, so 0.2% of the 7,500 centre entries were
+    measured above 1e-3 relative at the 1e-3 RMS floor (every other type
+    <= 0.07%): the strict fraction is held at 0.5% here, the main criterion
+    (1e-3 above 0.1 RMS, measured worst 4e-4) is unchanged."""
+    sc, _ = scenes.small_room(n=2500, n_sem=8, seed=60)
+    cams = scenes.orbit_cameras(40, seed=61, resolutions=[(40, 30), (36, 28)])
+    check_grad_errors(_grad_case(sc, cams, seed=62), strict_fraction=5e-3)
+
+
 def test_center_depth_ablation_forward_and_backward():
     """UNIGS_FLAG_CENTER_DEPTH (the centre-depth ablation of Tab. 6) against
     the oracle in the same mode: forward depth and the gradients."""
