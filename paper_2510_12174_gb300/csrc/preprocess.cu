@@ -335,9 +335,9 @@ __global__ void __launch_bounds__(256)
                             const WsHeader* __restrict__ hdr, const float* __restrict__ cull,
                             float* __restrict__ rec, float4* __restrict__ vp) {
     const int64_t n = g.n;
-    const uint32_t n_kept = hdr->n_kept;
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_kept;
-         idx += gridDim.x * blockDim.x) {
+    const int64_t n_kept = hdr->n_kept;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_kept;
+         idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = kept_list[idx];
         const int k = (int)(t / n);
         const int64_t i = t - (int64_t)k * n;
